@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the Dynamic Frontier PageRank update on GB300.
+
+One step = one batch through the whole hot path: dfpr_apply_batch (CSR/CSC
+update, real-change extraction) + dfpr_df_pagerank (marking, persistent
+frontier iteration). Default workload: R-MAT scale 24 (16.7M vertices, 268M
+edge draws, a, b, c, d = .57, .19, .19, .05), batches of 1e-4 |E| edges
+(80% uniform insertions, 20% deletions of existing edges), FP64 ranks,
+alpha = 0.85, tau = 1e-10, tau_f = tau / 1000. Ranks start from a converged
+static PageRank (untimed). Each timed step applies a new batch to the
+evolving graph; L2 is flushed (256 MiB write) between steps outside the
+events.
+
+Prints one JSON line (rank 0). --impl reference times the CPU oracle (one
+core) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "DF update ms/batch (apply_batch + df_pagerank)"
+UNIT = "ms/batch"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat14", "grid4096"], default="rmat24")
+    ap.add_argument("--batch-frac", type=float, default=1e-4)
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--mode", choices=["worklist", "round", "jacobi"], default="worklist")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-scale", type=int, default=18)
+    ap.add_argument("--timeout-ms", type=float, default=60000.0)
+    return ap.parse_args()
+
+
+WORKLOADS = {
+    "rmat24": dict(kind="rmat", scale=24, edge_factor=16, seed=3),
+    "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=3),
+    "rmat14": dict(kind="rmat", scale=14, edge_factor=16, seed=1),
+    "grid4096": dict(kind="grid", L=4096, seed=4),
+}
+
+
+def make_graph(spec):
+    if spec["kind"] == "rmat":
+        return workloads.rmat_graph(spec["scale"], spec["edge_factor"], spec["seed"])
+    return workloads.grid_graph(spec["L"], spec["seed"])
+
+
+def make_batch(spec, n, src, dst, b, seed):
+    if spec["kind"] == "rmat":
+        return workloads.uniform_batch(n, b, seed, src, dst)
+    return workloads.grid_local_batch(spec["L"], b, seed)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes of the persistent DF kernel (FP64 / FP32 ranks)
+# --------------------------------------------------------------------------
+
+def algorithmic_bytes(st, s_r: int) -> float:
+    """Bytes the method must move for the counted work:
+    per recomputed vertex: in-row descriptor (16 B), own rank read, rank and
+    contribution writes (3 s_R), out-row descriptor for its degree (16 B);
+    per gathered in-edge: id (4 B) + contribution (s_R); per expansion: the
+    out-row descriptor (16 B); per marked out-edge: id (4 B) + flag word RMW
+    (4 B); per queue insertion: slot write + read (8 B)."""
+    return (st["processed"] * (32 + 3 * s_r) + st["edges_gathered"] * (4 + s_r)
+            + st["expansions"] * 16 + st["edges_marked"] * 8 + st["pushes"] * 8)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# --------------------------------------------------------------------------
+
+def oracle_sample(scale: int, batch_frac: float, steps: int, seed0: int = 100):
+    """Times the oracle's apply + DF_LF (one core) on an R-MAT graph of the
+    given scale from the same generator; returns per-step ms and a description."""
+    import oracle
+    n, src, dst = workloads.rmat_graph(scale, 16, 3)
+    g = oracle.Graph.build(n, src, dst)
+    R, _ = g.static_bb(tol=1e-13)  # R^0 converged to the frontier tolerance
+    b = max(1, int(round(batch_frac * g.m)))
+    times = []
+    for i in range(steps):
+        batch = workloads.uniform_batch(n, b, seed0 + i, src, dst)
+        t0 = time.perf_counter()
+        g, _ = g.apply(*batch)
+        R, _ = g.df_lf(R)
+        times.append((time.perf_counter() - t0) * 1e3)
+    desc = (f"oracle apply + DF_LF (Alg. 2, one thread) on R-MAT scale {scale} "
+            f"(n={n}, m={g.m}), batches of {b} edges ({batch_frac:g}|E|, 80/20)")
+    return times, desc
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# --------------------------------------------------------------------------
+# arms
+# --------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    times, desc = oracle_sample(args.cpu_scale, args.batch_frac, args.warmup + args.steps)
+    timed = times[args.warmup:]
+    v = statistics.mean(timed)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"rmat{args.cpu_scale}-ef16-batch{args.batch_frac:g}",
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                         "cpu": cpu_model()},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2407_19562_gb300 as dfpr
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = WORKLOADS[args.workload]
+    n, src, dst = make_graph(spec)
+    cfg = dfpr.default_config(precision=dfpr.FP64 if args.precision == "fp64" else dfpr.FP32)
+    stream = torch.cuda.Stream(device=dev)  # the library and the events share it
+    torch.cuda.set_stream(stream)
+    g = dfpr.graph_load(n, src, dst, cfg, stream=stream.cuda_stream)
+    m0 = g.info()["m"]
+    tol = 1e-10 if args.precision == "fp64" else 1e-7
+    # R^0: static PageRank converged to the frontier tolerance (untimed), the
+    # state a sequence of DF updates maintains
+    st0 = dfpr.static_pagerank(g, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000.0,
+                                                      max_iter=1000))
+    if st0.status != dfpr.OK:
+        raise RuntimeError(f"static pagerank did not converge: {st0.as_dict()}")
+    b = max(1, int(round(args.batch_frac * m0)))
+    mode = {"worklist": dfpr.WORKLIST, "round": dfpr.ROUND, "jacobi": dfpr.JACOBI}[args.mode]
+    params = dfpr.default_params(mode=mode, tol=tol, timeout_ms=args.timeout_ms)
+    total = args.warmup + args.steps
+    batches = [make_batch(spec, n, src, dst, b, 100 + i + 1000 * rank) for i in range(total)]
+    dev_batches = [[torch.from_numpy(x).to(dev) for x in bt] for bt in batches]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        dfpr.apply_batch(g, *dev_batches[i])
+        dfpr.df_pagerank(g, params)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = dfpr.kernel_launches()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e0, e1 = ev[k]
+        e0.record()
+        dfpr.apply_batch(g, *dev_batches[args.warmup + k])
+        st = dfpr.df_pagerank(g, params)
+        e1.record()
+        stats.append(st.as_dict())
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = dfpr.kernel_launches() - launches0 - 0
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    my_total = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([my_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        my_total = float(t.item())
+    bad = [s for s in stats if s["status"] != dfpr.OK]
+
+    # roofline of the persistent DF kernel (the dominant kernel)
+    s_r = 8 if args.precision == "fp64" else 4
+    kern_ms = [s["ms"] for s in stats]
+    bytes_per = [algorithmic_bytes(s, s_r) for s in stats]
+    achieved = sum(bytes_per) / (sum(kern_ms) * 1e-3) / 1e9 if sum(kern_ms) > 0 else 0.0
+    peak, peak_kind = load_peaks()
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        e2e_batches = [make_batch(spec, n, src, dst, b, 50_000 + i + 1000 * rank)
+                       for i in range(args.steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for bt in e2e_batches:
+            dfpr.apply_batch(g, *bt)
+            dfpr.df_pagerank(g, params)
+            dfpr.get_ranks(g, host_out)
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        h2d = sum(x.nbytes for x in e2e_batches[0])
+        e2e = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(8 * n)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        times, desc = oracle_sample(args.cpu_scale, args.batch_frac, 2)
+        cpu = {"value": statistics.mean(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": desc, "cpu": cpu_model()}
+
+    if rank != 0:
+        return
+    value = my_total / (args.steps * ws)
+    mean = lambda k: float(np.mean([s[k] for s in stats]))  # noqa: E731
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": my_total / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}-batch{args.batch_frac:g}", "n": n, "m": m0,
+                   "batch_edges": b, "insert_frac": 0.8, "precision": args.precision,
+                   "mode": args.mode, "alpha": 0.85, "tol": tol,
+                   "l2": "flushed by a 256 MiB write between steps (outside the events)",
+                   "replicas": ws},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_worklist (persistent DF kernel)",
+                     "kernel_ms": float(np.mean(kern_ms)),
+                     "algorithmic_bytes_per_launch": float(np.mean(bytes_per))},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "work": {"processed": mean("processed"), "edges_gathered": mean("edges_gathered"),
+                 "expansions": mean("expansions"), "edges_marked": mean("edges_marked"),
+                 "pushes": mean("pushes"), "affected": mean("affected"),
+                 "apply_plus_df_ms_steps": step_ms, "wall_s": t_wall,
+                 "nonconverged_steps": len(bad)},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

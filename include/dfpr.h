@@ -1,0 +1,236 @@
+/*
+ * dfpr.h - Dynamic Frontier PageRank on one GPU (sm_103a), C ABI.
+ *
+ * The library keeps a directed graph resident in device memory, applies
+ * batches of edge deletions and insertions to it, and updates the PageRank
+ * vector incrementally with the Dynamic Frontier (DF) approach of
+ * arXiv 2407.19562 ("Lock-Free Computation of PageRank in Dynamic Graphs"):
+ * after a batch, the out-neighbours of every changed edge's source are marked
+ * affected (Sec. 4.1), their ranks are recomputed from their in-edges with
+ * Eq. 1, and any vertex whose rank moves by more than the frontier tolerance
+ * marks its own out-neighbours (Sec. 4.1, Alg. 1, Alg. 2), until every rank
+ * moves by at most the iteration tolerance.
+ *
+ * Conventions for every entry point:
+ *  - Vertex ids are int32 in [0, n). Edge counts and offsets are int64.
+ *  - Pointer arguments marked "host or device" are host pointers when
+ *    on_device == 0 and device pointers of the graph's device when
+ *    on_device != 0. The library copies inputs before returning; the caller
+ *    keeps ownership of every array it passes.
+ *  - The library owns all graph, rank and scratch memory. It allocates with
+ *    cudaMalloc unless an allocator was installed with dfpr_set_allocator.
+ *  - Work is issued on the graph's stream (given to dfpr_graph_load or
+ *    dfpr_graph_set_stream). Calls that return counts or statuses to the host
+ *    synchronise that stream before returning. Calls on one graph must not
+ *    overlap; distinct graphs may be used from distinct host threads.
+ *  - No entry point aborts, traps or exits. Failures return a status code and
+ *    leave a message for dfpr_last_error() (thread-local). A graph on which a
+ *    call failed with DFPR_ECUDA should be freed.
+ */
+#ifndef DFPR_H
+#define DFPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dfpr_graph dfpr_graph; /* opaque, owned by the library */
+
+typedef enum dfpr_status {
+  DFPR_OK = 0,
+  DFPR_EINVAL = 1,   /* bad argument: null pointer, id outside [0, n), bad size */
+  DFPR_ENOMEM = 2,   /* device or host allocation failed */
+  DFPR_ECUDA = 3,    /* a CUDA call failed; the message names it */
+  DFPR_ENOTCONV = 4, /* the iteration cap was reached before convergence */
+  DFPR_ETIMEOUT = 5, /* the time budget ran out; ranks are valid but unconverged */
+  DFPR_EBUSY = 6     /* another call on this graph is in progress */
+} dfpr_status;
+
+/* Rank storage and arithmetic. */
+enum {
+  DFPR_FP64 = 0, /* ranks and gather in FP64, as in the paper (Sec. 5.1.2) */
+  DFPR_FP32 = 1  /* ranks in FP32, compensated per-vertex sums, FP64 reductions */
+};
+
+/* Dead-end handling. */
+enum {
+  DFPR_SELF_LOOPS = 0, /* a self-loop on every vertex, kept through every batch
+                          (Sec. 5.1.3, Sec. 5.1.4); deleting a self-loop is a no-op */
+  DFPR_TELEPORT = 1    /* no self-loops added; the rank of dead ends is spread
+                          uniformly (alpha * D / n added to every vertex) */
+};
+
+/* Schedules of the rank iteration. */
+enum {
+  DFPR_MODE_WORKLIST = 0, /* persistent kernel fed by a device work queue: only
+                             vertices flagged not-converged are recomputed,
+                             in place, with no grid-wide barrier */
+  DFPR_MODE_ROUND = 1,    /* Alg. 2 schedule: every affected vertex is recomputed
+                             in each pass, in place, chunks claimed dynamically
+                             per pass, no grid-wide barrier */
+  DFPR_MODE_JACOBI = 2    /* Alg. 1 / Alg. 3 schedule: two rank vectors and an
+                             L-inf reduction per iteration (barrier-based) */
+};
+
+/* Graph options fixed at load time. */
+typedef struct dfpr_graph_config {
+  int32_t precision;  /* DFPR_FP64 (default) or DFPR_FP32 */
+  int32_t dead_end;   /* DFPR_SELF_LOOPS (default) or DFPR_TELEPORT */
+  double row_slack;   /* extra capacity per row as a fraction of its degree, so
+                         batches update rows in place (default 0.125) */
+  int32_t min_slack;  /* minimum extra capacity per row (default 2) */
+  int32_t reserved;
+  double tail_slack;  /* spare edge capacity for rows that outgrow their slot,
+                         as a fraction of the edge count (default 0.125) */
+} dfpr_graph_config;
+
+/* Parameters of one rank computation (defaults: the paper's, Sec. 5.1.2, 4.5). */
+typedef struct dfpr_params {
+  double alpha;        /* damping factor (0.85) */
+  double tol;          /* iteration tolerance tau, per-vertex change (1e-10);
+                          in FP32 mode a relative tolerance (change <= tol * R[v]) */
+  double frontier_tol; /* frontier tolerance tau_f; <= 0 selects tol / 1000 (Sec. 4.5);
+                          relative in FP32 mode */
+  int32_t max_iter;    /* MAX_ITERATIONS (500): iterations or passes; in worklist
+                          mode the cap is max_iter * n recomputations in total */
+  int32_t mode;        /* DFPR_MODE_* */
+  int32_t normalize;   /* 1: rescale ranks to sum 1 (FP64 sum) after convergence */
+  int32_t grid_ctas;   /* persistent grid size; 0 = one wave on every SM */
+  double timeout_ms;   /* wall-clock budget on the device; <= 0 means 60000 */
+} dfpr_params;
+
+/* Counters of one call. */
+typedef struct dfpr_stats {
+  int64_t processed;      /* vertex rank recomputations */
+  int64_t edges_gathered; /* in-edges read by those recomputations */
+  int64_t expansions;     /* recomputations whose change exceeded tau_f */
+  int64_t edges_marked;   /* out-edges visited by marking and expansion */
+  int64_t pushes;         /* work-queue insertions (worklist mode) */
+  int64_t affected;       /* distinct vertices recomputed at least once */
+  int32_t passes;         /* iterations (jacobi) or passes (round); 0 for worklist */
+  int32_t status;         /* dfpr_status of the call */
+  double residual_linf;   /* jacobi: last L-inf iterate difference; else max last change */
+  double rank_sum;        /* FP64 sum of the ranks after the call when normalize = 1,
+                             else NaN */
+  double ms;              /* device time (CUDA events): the persistent kernel alone in
+                             worklist mode, all kernels of the call otherwise */
+} dfpr_stats;
+
+/* Fills *cfg / *p with the defaults listed above. */
+void dfpr_default_config(dfpr_graph_config* cfg);
+void dfpr_default_params(dfpr_params* p);
+
+/*
+ * Builds the snapshot G^0 from m raw edges src[i] -> dst[i] (host or device;
+ * duplicates allowed; ids in [0, n)): out-rows (CSR) and in-rows (CSC) with
+ * sorted unique rows, self-loops added under DFPR_SELF_LOOPS (Sec. 5.1.3).
+ * Ranks start at 1/n (Sec. 3.1). cuda_stream is a cudaStream_t (NULL: the
+ * library creates one). cfg NULL selects the defaults. On success *out owns
+ * the graph until dfpr_graph_free. Errors: EINVAL (n <= 0, m < 0, null
+ * arrays with m > 0, an id out of range), ENOMEM, ECUDA.
+ */
+dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                            int on_device, void* cuda_stream, const dfpr_graph_config* cfg,
+                            dfpr_graph** out);
+
+/* Releases every device and host resource of g (NULL is a no-op). */
+dfpr_status dfpr_graph_free(dfpr_graph* g);
+
+/* Makes later calls on g issue their work on cuda_stream (a cudaStream_t). */
+dfpr_status dfpr_graph_set_stream(dfpr_graph* g, void* cuda_stream);
+
+/* n, current edge count m (self-loops included) and device id of g. */
+dfpr_status dfpr_graph_info(const dfpr_graph* g, int32_t* n, int64_t* m, int32_t* device);
+
+/*
+ * Applies a batch update (Sec. 3.4): G^t = (G^{t-1} minus deletions) plus
+ * insertions, deletions taken first. Duplicate entries collapse; deleting an
+ * absent edge, inserting a present edge and (DFPR_SELF_LOOPS) deleting a
+ * self-loop are no-ops, not errors. Rows stay sorted and unique. The real
+ * changes Delta- = E^{t-1} \ E^t and Delta+ = E^t \ E^{t-1} are kept for the
+ * next dfpr_df_pagerank, which marks the out-neighbours of their sources
+ * (Sec. 4.1). n_applied (host, may be NULL) receives {|Delta-|, |Delta+|}.
+ * Arrays are host or device. Applying a second batch before dfpr_df_pagerank
+ * merges both into the pending change set. Errors: EINVAL (an id out of range;
+ * the graph is left unchanged), ENOMEM, ECUDA, EBUSY.
+ */
+dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_src,
+                             const int32_t* del_dst, int64_t n_ins, const int32_t* ins_src,
+                             const int32_t* ins_dst, int on_device, int64_t* n_applied);
+
+/*
+ * Dynamic Frontier update (Sec. 4; Alg. 1 for DFPR_MODE_JACOBI, Alg. 2 for
+ * DFPR_MODE_ROUND, the work-queue schedule for DFPR_MODE_WORKLIST): starting
+ * from the current ranks R^{t-1}, marks the affected vertices of the pending
+ * change set and iterates Eq. 1 over them until convergence, in place. Clears
+ * the pending change set. With no pending changes it returns at once with 0
+ * recomputations. p NULL selects the defaults; stats may be NULL.
+ * Returns ENOTCONV / ETIMEOUT when the cap / budget stopped the iteration
+ * (ranks are then valid but not converged), EINVAL for bad parameters.
+ */
+dfpr_status dfpr_df_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats);
+
+/*
+ * Naive-dynamic update (Sec. 3.5.1; Alg. 5 / Alg. 6): iterates Eq. 1 over
+ * every vertex starting from the current ranks. Clears the pending change set.
+ */
+dfpr_status dfpr_nd_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats);
+
+/*
+ * Static PageRank (Sec. 3.3; Alg. 3 / Alg. 4): resets every rank to 1/n and
+ * iterates Eq. 1 over every vertex until convergence. Clears the pending
+ * change set.
+ */
+dfpr_status dfpr_static_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats);
+
+/* Copies the n ranks out as FP64 (host or device; FP32 ranks are widened). */
+dfpr_status dfpr_get_ranks(const dfpr_graph* g, double* out, int on_device);
+
+/* Replaces the n ranks (host or device FP64), e.g. to resume from saved ranks. */
+dfpr_status dfpr_set_ranks(dfpr_graph* g, const double* ranks, int on_device);
+
+/*
+ * Copies the graph out in packed form (host or device): offsets[n + 1]
+ * (int64) and idx[m] (int32); out-rows (CSR) for dfpr_get_csr, in-rows (CSC)
+ * for dfpr_get_csc. Rows are sorted ascending; self-loops included.
+ */
+dfpr_status dfpr_get_csr(const dfpr_graph* g, int64_t* offsets, int32_t* idx, int on_device);
+dfpr_status dfpr_get_csc(const dfpr_graph* g, int64_t* offsets, int32_t* idx, int on_device);
+
+/*
+ * Initial marking of the DF approach (Sec. 4.1; Alg. 1 and Alg. 2 marking
+ * loops) for the pending change set, without updating ranks or clearing the
+ * set: affected[v] (n bytes, host or device) is 1 when v is an out-neighbour,
+ * in G^{t-1} or G^t, of the source of a real change (with self-loops, the
+ * source itself). Returns the count in *count (host, may be NULL).
+ */
+dfpr_status dfpr_initial_affected(dfpr_graph* g, uint8_t* affected, int on_device,
+                                  int64_t* count);
+
+/*
+ * Installs the device allocator used for all later allocations (NULL, NULL
+ * restores cudaMalloc / cudaFree). alloc(bytes, stream, ctx) returns a device
+ * pointer or NULL; free(ptr, bytes, stream, ctx) releases it. Memory already
+ * held by existing graphs is returned through the allocator that provided it.
+ */
+typedef void* (*dfpr_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*dfpr_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+dfpr_status dfpr_set_allocator(dfpr_alloc_fn alloc, dfpr_free_fn free_fn, void* ctx);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* dfpr_last_error(void);
+
+/* Number of CUDA kernels the library has launched in this process so far
+ * (a diagnostic counter; no paper counterpart). */
+int64_t dfpr_kernel_launches(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t dfpr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFPR_H */

@@ -1,0 +1,408 @@
+"""Python binding of libdfpr (Dynamic Frontier PageRank on GB300, sm_103a).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name in ``include/dfpr.h`` (``graph_load`` -> ``dfpr_graph_load`` ...).
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); all arrays
+of one call must live on the same side. There is no CPU fallback: if the CUDA
+library cannot be built or loaded, ``load()`` raises.
+
+Hard failures (bad arguments, CUDA errors, out of memory, busy graph) raise
+``DfprError``. A rank computation stopped by its iteration cap or time budget
+returns its stats with ``status`` set to ``ENOTCONV`` / ``ETIMEOUT``; the
+ranks are valid but not converged.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "DfprError", "Config", "Params", "Stats", "Graph", "load", "version", "last_error",
+    "kernel_launches",
+    "default_config", "default_params", "graph_load", "graph_free", "graph_info",
+    "graph_set_stream", "apply_batch", "df_pagerank", "nd_pagerank", "static_pagerank",
+    "get_ranks", "set_ranks", "get_csr", "get_csc", "initial_affected", "set_allocator",
+    "use_torch_allocator", "OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "EBUSY",
+    "FP64", "FP32", "SELF_LOOPS", "TELEPORT", "WORKLIST", "ROUND", "JACOBI",
+]
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, EBUSY = range(7)
+FP64, FP32 = 0, 1
+SELF_LOOPS, TELEPORT = 0, 1
+WORKLIST, ROUND, JACOBI = 0, 1, 2
+_STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "EBUSY"]
+
+
+class DfprError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        name = _STATUS_NAMES[status] if 0 <= status < len(_STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {message}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("dead_end", ctypes.c_int32),
+                ("row_slack", ctypes.c_double), ("min_slack", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tail_slack", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("tol", ctypes.c_double),
+                ("frontier_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("normalize", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("processed", ctypes.c_int64), ("edges_gathered", ctypes.c_int64),
+                ("expansions", ctypes.c_int64), ("edges_marked", ctypes.c_int64),
+                ("pushes", ctypes.c_int64), ("affected", ctypes.c_int64),
+                ("passes", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("residual_linf", ctypes.c_double), ("rank_sum", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                           ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+_keep = []  # callbacks installed with set_allocator
+
+
+def load():
+    """Builds (if stale) and loads libdfpr.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, ci = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+        st = ctypes.c_int
+        sig = {
+            "dfpr_default_config": (None, [ctypes.POINTER(Config)]),
+            "dfpr_default_params": (None, [ctypes.POINTER(Params)]),
+            "dfpr_graph_load": (st, [i32, i64, vp, vp, ci, vp, ctypes.POINTER(Config),
+                                     ctypes.POINTER(vp)]),
+            "dfpr_graph_free": (st, [vp]),
+            "dfpr_graph_set_stream": (st, [vp, vp]),
+            "dfpr_graph_info": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                     ctypes.POINTER(i32)]),
+            "dfpr_apply_batch": (st, [vp, i64, vp, vp, i64, vp, vp, ci, ctypes.POINTER(i64)]),
+            "dfpr_df_pagerank": (st, [vp, ctypes.POINTER(Params), ctypes.POINTER(Stats)]),
+            "dfpr_nd_pagerank": (st, [vp, ctypes.POINTER(Params), ctypes.POINTER(Stats)]),
+            "dfpr_static_pagerank": (st, [vp, ctypes.POINTER(Params), ctypes.POINTER(Stats)]),
+            "dfpr_get_ranks": (st, [vp, vp, ci]),
+            "dfpr_set_ranks": (st, [vp, vp, ci]),
+            "dfpr_get_csr": (st, [vp, vp, vp, ci]),
+            "dfpr_get_csc": (st, [vp, vp, vp, ci]),
+            "dfpr_initial_affected": (st, [vp, vp, ci, ctypes.POINTER(i64)]),
+            "dfpr_set_allocator": (st, [ALLOC_FN, FREE_FN, vp]),
+            "dfpr_last_error": (ctypes.c_char_p, []),
+            "dfpr_version": (i32, []),
+            "dfpr_kernel_launches": (i64, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def version() -> int:
+    return int(load().dfpr_version())
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().dfpr_kernel_launches())
+
+
+def last_error() -> str:
+    return (load().dfpr_last_error() or b"").decode(errors="replace")
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise DfprError(rc, where, last_error())
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    load().dfpr_default_config(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().dfpr_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# --------------------------------------------------------------------------
+# array marshalling
+# --------------------------------------------------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype, n_expected=None, name="array"):
+    """(pointer, length, on_device) of a numpy array or torch tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        import torch
+        tdt = {np.int32: torch.int32, np.float64: torch.float64, np.int64: torch.int64,
+               np.uint8: torch.uint8}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            raise DfprError(EINVAL, name, f"need a contiguous {tdt} tensor")
+        n = x.numel()
+        on_dev = 1 if x.is_cuda else 0
+        ptr = x.data_ptr()
+    else:
+        if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+            raise DfprError(EINVAL, name, f"need a contiguous numpy {np.dtype(dtype)} array")
+        n = x.size
+        on_dev = 0
+        ptr = x.ctypes.data
+    if n_expected is not None and n != n_expected:
+        raise DfprError(EINVAL, name, f"expected {n_expected} elements, got {n}")
+    return (ptr if n else None), n, on_dev
+
+
+def _side(*sides):
+    s = {x for x in sides if x is not None}
+    if len(s) > 1:
+        raise DfprError(EINVAL, "arrays", "all arrays of one call must be on the same side")
+    return s.pop() if s else 0
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # noqa: BLE001 - torch is optional plumbing
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------
+# graph handle
+# --------------------------------------------------------------------------
+
+class Graph:
+    """Owns a dfpr_graph*; freed by graph_free() or on garbage collection."""
+
+    def __init__(self, handle: int, n: int):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise DfprError(EINVAL, "graph", "graph was freed")
+        return self._h
+
+    def free(self):
+        h, self._h = self._h, None
+        if h:
+            _check(load().dfpr_graph_free(h), "graph_free")
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    # convenience methods mirroring the module functions
+    def apply_batch(self, *a, **k):
+        return apply_batch(self, *a, **k)
+
+    def df_pagerank(self, *a, **k):
+        return df_pagerank(self, *a, **k)
+
+    def nd_pagerank(self, *a, **k):
+        return nd_pagerank(self, *a, **k)
+
+    def static_pagerank(self, *a, **k):
+        return static_pagerank(self, *a, **k)
+
+    def get_ranks(self, *a, **k):
+        return get_ranks(self, *a, **k)
+
+    def set_ranks(self, *a, **k):
+        return set_ranks(self, *a, **k)
+
+    def get_csr(self, *a, **k):
+        return get_csr(self, *a, **k)
+
+    def get_csc(self, *a, **k):
+        return get_csc(self, *a, **k)
+
+    def initial_affected(self, *a, **k):
+        return initial_affected(self, *a, **k)
+
+    def info(self):
+        return graph_info(self)
+
+
+def graph_load(n: int, src, dst, config: Config | None = None, stream="torch") -> Graph:
+    """dfpr_graph_load. stream: a cudaStream_t (int), None for a library-owned
+    stream, or "torch" for torch's current stream when torch has initialised CUDA."""
+    lib = load()
+    ps, ms, ds = _ptr(src, np.int32, name="src")
+    pd, md, dd = _ptr(dst, np.int32, name="dst")
+    if ms != md:
+        raise DfprError(EINVAL, "graph_load", "src and dst lengths differ")
+    on_dev = _side(ds, dd)
+    s = _torch_stream() if stream == "torch" else stream
+    h = ctypes.c_void_p()
+    _check(lib.dfpr_graph_load(int(n), ms, ps, pd, on_dev, s,
+                               ctypes.byref(config) if config is not None else None,
+                               ctypes.byref(h)), "graph_load")
+    return Graph(h.value, int(n))
+
+
+def graph_free(g: Graph):
+    g.free()
+
+
+def graph_set_stream(g: Graph, stream):
+    _check(load().dfpr_graph_set_stream(g.handle, stream), "graph_set_stream")
+
+
+def graph_info(g: Graph):
+    n, m, dev = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    _check(load().dfpr_graph_info(g.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(dev)),
+           "graph_info")
+    return {"n": n.value, "m": m.value, "device": dev.value}
+
+
+def apply_batch(g: Graph, del_src, del_dst, ins_src, ins_dst):
+    """dfpr_apply_batch -> (real deletions, real insertions)."""
+    a = [_ptr(x, np.int32, name=nm) for x, nm in
+         ((del_src, "del_src"), (del_dst, "del_dst"), (ins_src, "ins_src"), (ins_dst, "ins_dst"))]
+    if a[0][1] != a[1][1] or a[2][1] != a[3][1]:
+        raise DfprError(EINVAL, "apply_batch", "source and target lengths differ")
+    on_dev = _side(*(x[2] for x in a))
+    out = (ctypes.c_int64 * 2)()
+    _check(load().dfpr_apply_batch(g.handle, a[0][1], a[0][0], a[1][0], a[2][1], a[2][0],
+                                   a[3][0], on_dev, out), "apply_batch")
+    return int(out[0]), int(out[1])
+
+
+def _run(fn, where, g, params):
+    st = Stats()
+    p = params if params is not None else default_params()
+    rc = fn(g.handle, ctypes.byref(p), ctypes.byref(st))
+    if rc not in (OK, ENOTCONV, ETIMEOUT):
+        _check(rc, where)
+    st.status = rc
+    return st
+
+
+def df_pagerank(g: Graph, params: Params | None = None) -> Stats:
+    return _run(load().dfpr_df_pagerank, "df_pagerank", g, params)
+
+
+def nd_pagerank(g: Graph, params: Params | None = None) -> Stats:
+    return _run(load().dfpr_nd_pagerank, "nd_pagerank", g, params)
+
+
+def static_pagerank(g: Graph, params: Params | None = None) -> Stats:
+    return _run(load().dfpr_static_pagerank, "static_pagerank", g, params)
+
+
+def get_ranks(g: Graph, out=None):
+    """dfpr_get_ranks into `out` (numpy float64 or torch float64, host or CUDA);
+    returns a new numpy array when out is None."""
+    if out is None:
+        out = np.empty(g.n, np.float64)
+    p, _, dev = _ptr(out, np.float64, g.n, "out")
+    _check(load().dfpr_get_ranks(g.handle, p, dev), "get_ranks")
+    return out
+
+
+def set_ranks(g: Graph, ranks):
+    p, _, dev = _ptr(ranks, np.float64, g.n, "ranks")
+    _check(load().dfpr_set_ranks(g.handle, p, dev), "set_ranks")
+
+
+def _export(fn, where, g, offsets, idx):
+    info = graph_info(g)
+    if offsets is None:
+        offsets = np.empty(info["n"] + 1, np.int64)
+    if idx is None:
+        idx = np.empty(max(info["m"], 1), np.int32)[:info["m"]]
+    po, _, d1 = _ptr(offsets, np.int64, info["n"] + 1, "offsets")
+    pi, _, d2 = _ptr(idx, np.int32, info["m"], "idx")
+    if pi is None:  # empty graph: give a valid pointer
+        keep = np.empty(1, np.int32)
+        pi = keep.ctypes.data
+    _check(fn(g.handle, po, pi, _side(d1, d2)), where)
+    return offsets, idx
+
+
+def get_csr(g: Graph, offsets=None, idx=None):
+    return _export(load().dfpr_get_csr, "get_csr", g, offsets, idx)
+
+
+def get_csc(g: Graph, offsets=None, idx=None):
+    return _export(load().dfpr_get_csc, "get_csc", g, offsets, idx)
+
+
+def initial_affected(g: Graph, out=None):
+    """dfpr_initial_affected -> (flags uint8[n], count)."""
+    if out is None:
+        out = np.zeros(g.n, np.uint8)
+    p, _, dev = _ptr(out, np.uint8, g.n, "out")
+    cnt = ctypes.c_int64()
+    _check(load().dfpr_initial_affected(g.handle, p, dev, ctypes.byref(cnt)), "initial_affected")
+    return out, int(cnt.value)
+
+
+def set_allocator(alloc=None, free=None, ctx=None):
+    """dfpr_set_allocator with Python callables alloc(bytes, stream) -> int and
+    free(ptr, bytes, stream); None, None restores cudaMalloc."""
+    lib = load()
+    if alloc is None and free is None:
+        _check(lib.dfpr_set_allocator(ALLOC_FN(), FREE_FN(), None), "set_allocator")
+        return
+    a = ALLOC_FN(lambda nbytes, stream, _c: alloc(nbytes, stream) or None)
+    f = FREE_FN(lambda ptr, nbytes, stream, _c: free(ptr, nbytes, stream))
+    _keep.extend([a, f])
+    _check(lib.dfpr_set_allocator(a, f, ctx), "set_allocator")
+
+
+def use_torch_allocator():
+    """Routes the library's device allocations through torch's caching allocator."""
+    import torch
+
+    def alloc(nbytes, stream):
+        try:
+            s = torch.cuda.ExternalStream(stream) if stream else None
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=s)
+        except Exception:  # noqa: BLE001 - reported to the library as NULL
+            return None
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    set_allocator(alloc, free)

@@ -1,0 +1,521 @@
+// C ABI of libdfpr (declared in include/dfpr.h): argument checks, device and
+// stream handling, host <-> device staging and status codes. Every entry
+// point catches the library's internal failures and returns a status.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "df.cuh"
+#include "graph.cuh"
+#include "primitives.cuh"
+
+namespace dfpr {
+
+namespace {
+thread_local std::string t_err;
+std::mutex g_alloc_mu;
+dfpr_alloc_fn g_alloc = nullptr;
+dfpr_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+}  // namespace
+
+std::atomic<long long> g_launches{0};
+
+void set_error(const std::string& msg) { t_err = msg; }
+const char* get_error() { return t_err.c_str(); }
+
+void* dev_alloc(size_t bytes, cudaStream_t s, FreeRec* rec) {
+  dfpr_alloc_fn fa;
+  FreeRec r;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    fa = g_alloc;
+    r.fn = g_free;
+    r.ctx = g_alloc_ctx;
+  }
+  void* p = nullptr;
+  if (fa) {
+    p = fa(bytes, (void*)s, r.ctx);
+  } else {
+    r.fn = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (!p) {
+    set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
+    throw Fail{DFPR_ENOMEM};
+  }
+  *rec = r;
+  return p;
+}
+
+void dev_free(void* p, size_t bytes, cudaStream_t s, const FreeRec& rec) {
+  if (!p) return;
+  if (rec.fn) rec.fn(p, bytes, (void*)s, rec.ctx);
+  else cudaFree(p);
+}
+
+namespace {
+
+constexpr int kNT = 256;
+
+#define GRID_STRIDE(i, n)                                                             \
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
+       i += (long long)gridDim.x * blockDim.x)
+
+__global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, long long n) {
+  GRID_STRIDE(i, n) out[i] = (double)in[i];
+}
+__global__ void k_narrow(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  GRID_STRIDE(i, n) out[i] = (float)in[i];
+}
+
+// Makes the graph's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) DFPR_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// One call at a time per graph.
+struct BusyGuard {
+  dfpr_graph* g;
+  explicit BusyGuard(dfpr_graph* gr) : g(gr) {
+    int z = 0;
+    if (!g->busy.compare_exchange_strong(z, 1)) {
+      g = nullptr;
+      set_error("another call on this graph is in progress");
+      throw Fail{DFPR_EBUSY};
+    }
+  }
+  ~BusyGuard() {
+    if (g) g->busy.store(0);
+  }
+};
+
+// Device copy of a caller array (or the caller's device pointer itself).
+template <class T>
+const T* stage_in(dfpr_graph* g, DevArray<T>& tmp, const T* p, long long n, int on_device) {
+  if (n <= 0) return nullptr;
+  if (on_device) return p;
+  tmp.reset((size_t)n, g->stream);
+  DFPR_CUDA(cudaMemcpyAsync(tmp.p, p, sizeof(T) * n, cudaMemcpyHostToDevice, g->stream));
+  return tmp.p;
+}
+
+void check_params(const dfpr_params& p) {
+  DFPR_REQUIRE(p.alpha > 0.0 && p.alpha < 1.0, DFPR_EINVAL, "alpha must lie in (0, 1)");
+  DFPR_REQUIRE(p.tol > 0.0 && std::isfinite(p.tol), DFPR_EINVAL, "tol must be positive");
+  DFPR_REQUIRE(p.max_iter >= 1, DFPR_EINVAL, "max_iter must be >= 1");
+  DFPR_REQUIRE(p.mode >= DFPR_MODE_WORKLIST && p.mode <= DFPR_MODE_JACOBI, DFPR_EINVAL,
+               "unknown mode");
+  DFPR_REQUIRE(p.grid_ctas >= 0, DFPR_EINVAL, "grid_ctas must be >= 0");
+}
+
+
+dfpr_status run_call(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, RunKind kind) {
+  dfpr_params p;
+  if (pp) p = *pp;
+  else dfpr_default_params(&p);
+  check_params(p);
+  if (g->cfg.dead_end == DFPR_TELEPORT)
+    DFPR_REQUIRE(kind != kRunDF && p.mode == DFPR_MODE_JACOBI, DFPR_EINVAL,
+                 "teleport dead-end handling is supported by the jacobi static / naive-dynamic "
+                 "schedules only");
+  dfpr_stats local;
+  memset(&local, 0, sizeof local);
+  local.rank_sum = NAN;
+  if (kind == kRunDF && g->pend.n_src == 0 && g->pend.n_dst == 0) {
+    if (st) *st = local;
+    return DFPR_OK;
+  }
+  dfpr_status r = run_iteration(g, p, kind, &local);
+  if (p.normalize && r == DFPR_OK) local.rank_sum = rank_sum(g);
+  if (st) *st = local;
+  if (r != DFPR_OK)
+    set_error(r == DFPR_ETIMEOUT ? "the time budget ran out before convergence"
+                                 : "the iteration cap was reached before convergence");
+  return r;
+}
+
+}  // namespace
+}  // namespace dfpr
+
+using namespace dfpr;
+
+#define API_BEGIN try {
+#define API_END                                              \
+  }                                                          \
+  catch (const Fail& f) {                                    \
+    return f.st;                                             \
+  }                                                          \
+  catch (const std::bad_alloc&) {                            \
+    set_error("host allocation failed");                     \
+    return DFPR_ENOMEM;                                      \
+  }                                                          \
+  catch (...) {                                              \
+    set_error("unexpected internal error");                  \
+    return DFPR_ECUDA;                                       \
+  }
+
+extern "C" {
+
+void dfpr_default_config(dfpr_graph_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->precision = DFPR_FP64;
+  cfg->dead_end = DFPR_SELF_LOOPS;
+  cfg->row_slack = 0.125;
+  cfg->min_slack = 2;
+  cfg->tail_slack = 0.125;
+}
+
+void dfpr_default_params(dfpr_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->alpha = 0.85;
+  p->tol = 1e-10;
+  p->frontier_tol = 0.0;
+  p->max_iter = 500;
+  p->mode = DFPR_MODE_WORKLIST;
+  p->normalize = 0;
+  p->grid_ctas = 0;
+  p->timeout_ms = 60000.0;
+}
+
+int32_t dfpr_version(void) { return 100; }
+
+int64_t dfpr_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+const char* dfpr_last_error(void) { return get_error(); }
+
+dfpr_status dfpr_set_allocator(dfpr_alloc_fn alloc, dfpr_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    set_error("dfpr_set_allocator: give both functions or neither");
+    return DFPR_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return DFPR_OK;
+}
+
+dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                            int on_device, void* cuda_stream, const dfpr_graph_config* cfg,
+                            dfpr_graph** out) {
+  set_error("");
+  if (!out) {
+    set_error("dfpr_graph_load: out is NULL");
+    return DFPR_EINVAL;
+  }
+  *out = nullptr;
+  if (n <= 0 || m < 0 || (m > 0 && (!src || !dst))) {
+    set_error("dfpr_graph_load: need n > 0, m >= 0 and edge arrays when m > 0");
+    return DFPR_EINVAL;
+  }
+  dfpr_graph_config c;
+  if (cfg) c = *cfg;
+  else dfpr_default_config(&c);
+  if ((c.precision != DFPR_FP64 && c.precision != DFPR_FP32) ||
+      (c.dead_end != DFPR_SELF_LOOPS && c.dead_end != DFPR_TELEPORT) || c.row_slack < 0 ||
+      c.min_slack < 0 || c.tail_slack < 0) {
+    set_error("dfpr_graph_load: invalid config");
+    return DFPR_EINVAL;
+  }
+  dfpr_graph* g = nullptr;
+  API_BEGIN
+  g = new dfpr_graph();
+  g->cfg = c;
+  g->n = n;
+  g->bits = id_bits(n);
+  DFPR_CUDA(cudaGetDevice(&g->device));
+  DFPR_CUDA(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device));
+  if (cuda_stream) {
+    g->stream = (cudaStream_t)cuda_stream;
+  } else {
+    DFPR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    g->own_stream = true;
+  }
+  DFPR_CUDA(cudaMallocHost(&g->pinned, 16 * sizeof(unsigned long long)));
+  g->host_sync.reset(16, g->stream);
+  DFPR_CUDA(cudaMemsetAsync(g->host_sync.p, 0, 16 * sizeof(unsigned long long), g->stream));
+  {
+    DevArray<int32_t> ts, td;
+    const int32_t* ds = stage_in(g, ts, src, m, on_device);
+    const int32_t* dd = stage_in(g, td, dst, m, on_device);
+    graph_build(g, ds, dd, m);
+    DFPR_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  alloc_iteration_state(g);
+  reset_ranks(g);
+  DFPR_CUDA(cudaStreamSynchronize(g->stream));
+  *out = g;
+  return DFPR_OK;
+  }
+  catch (const Fail& f) {
+    if (g) dfpr_graph_free(g);
+    return f.st;
+  }
+  catch (const std::bad_alloc&) {
+    if (g) dfpr_graph_free(g);
+    set_error("host allocation failed");
+    return DFPR_ENOMEM;
+  }
+  catch (...) {
+    if (g) dfpr_graph_free(g);
+    set_error("unexpected internal error");
+    return DFPR_ECUDA;
+  }
+}
+
+dfpr_status dfpr_graph_free(dfpr_graph* g) {
+  if (!g) return DFPR_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != g->device) cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  cudaStream_t s = g->stream;
+  const bool own = g->own_stream;
+  unsigned long long* pinned = g->pinned;
+  delete g;  // device arrays are released by their destructors
+  if (pinned) cudaFreeHost(pinned);
+  if (own && s) cudaStreamDestroy(s);
+  if (prev >= 0) cudaSetDevice(prev);
+  return DFPR_OK;
+}
+
+dfpr_status dfpr_graph_set_stream(dfpr_graph* g, void* cuda_stream) {
+  if (!g) {
+    set_error("graph is NULL");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  DFPR_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->own_stream) {
+    DFPR_CUDA(cudaStreamDestroy(g->stream));
+    g->own_stream = false;
+  }
+  if (cuda_stream) {
+    g->stream = (cudaStream_t)cuda_stream;
+  } else {
+    DFPR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    g->own_stream = true;
+  }
+  return DFPR_OK;
+  API_END
+}
+
+dfpr_status dfpr_graph_info(const dfpr_graph* g, int32_t* n, int64_t* m, int32_t* device) {
+  if (!g) {
+    set_error("graph is NULL");
+    return DFPR_EINVAL;
+  }
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (device) *device = g->device;
+  return DFPR_OK;
+}
+
+dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_src,
+                             const int32_t* del_dst, int64_t n_ins, const int32_t* ins_src,
+                             const int32_t* ins_dst, int on_device, int64_t* n_applied) {
+  if (n_applied) n_applied[0] = n_applied[1] = 0;
+  if (!g || n_del < 0 || n_ins < 0 || (n_del > 0 && (!del_src || !del_dst)) ||
+      (n_ins > 0 && (!ins_src || !ins_dst))) {
+    set_error("dfpr_apply_batch: invalid arguments");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  DevArray<int32_t> a, b, c, d;
+  const int32_t* ds = stage_in(g, a, del_src, n_del, on_device);
+  const int32_t* dd = stage_in(g, b, del_dst, n_del, on_device);
+  const int32_t* is = stage_in(g, c, ins_src, n_ins, on_device);
+  const int32_t* id = stage_in(g, d, ins_dst, n_ins, on_device);
+  long long applied[2] = {0, 0};
+  graph_apply(g, ds, dd, n_del, is, id, n_ins, applied);
+  DFPR_CUDA(cudaStreamSynchronize(g->stream));
+  if (n_applied) {
+    n_applied[0] = applied[0];
+    n_applied[1] = applied[1];
+  }
+  return DFPR_OK;
+  API_END
+}
+
+dfpr_status dfpr_df_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats) {
+  if (!g) {
+    set_error("graph is NULL");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  return run_call(g, p, stats, kRunDF);
+  API_END
+}
+
+dfpr_status dfpr_nd_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats) {
+  if (!g) {
+    set_error("graph is NULL");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  return run_call(g, p, stats, kRunND);
+  API_END
+}
+
+dfpr_status dfpr_static_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats) {
+  if (!g) {
+    set_error("graph is NULL");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  return run_call(g, p, stats, kRunStatic);
+  API_END
+}
+
+dfpr_status dfpr_get_ranks(const dfpr_graph* gc, double* out, int on_device) {
+  if (!gc || !out) {
+    set_error("dfpr_get_ranks: NULL argument");
+    return DFPR_EINVAL;
+  }
+  dfpr_graph* g = const_cast<dfpr_graph*>(gc);
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->stream;
+  const long long n = g->n;
+  if (g->cfg.precision == DFPR_FP64) {
+    DFPR_CUDA(cudaMemcpyAsync(out, g->R64.p, sizeof(double) * n,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  } else {
+    DevArray<double> tmp;
+    double* dst = out;
+    if (!on_device) {
+      tmp.reset((size_t)n, s);
+      dst = tmp.p;
+    }
+    k_widen<<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(g->R32.p, dst, n);
+    DFPR_LAUNCHED();
+    if (!on_device)
+      DFPR_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    DFPR_CUDA(cudaStreamSynchronize(s));
+  }
+  DFPR_CUDA(cudaStreamSynchronize(s));
+  return DFPR_OK;
+  API_END
+}
+
+dfpr_status dfpr_set_ranks(dfpr_graph* g, const double* ranks, int on_device) {
+  if (!g || !ranks) {
+    set_error("dfpr_set_ranks: NULL argument");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->stream;
+  const long long n = g->n;
+  if (g->cfg.precision == DFPR_FP64) {
+    DFPR_CUDA(cudaMemcpyAsync(g->R64.p, ranks, sizeof(double) * n,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else {
+    DevArray<double> tmp;
+    const double* srcp = stage_in(g, tmp, ranks, n, on_device);
+    k_narrow<<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(srcp, g->R32.p, n);
+    DFPR_LAUNCHED();
+  }
+  refresh_contributions(g);
+  DFPR_CUDA(cudaStreamSynchronize(s));
+  return DFPR_OK;
+  API_END
+}
+
+static dfpr_status export_dir(const dfpr_graph* gc, bool csr, int64_t* offsets, int32_t* idx,
+                              int on_device) {
+  if (!gc || !offsets || !idx) {
+    set_error("dfpr_get_csr/csc: NULL argument");
+    return DFPR_EINVAL;
+  }
+  dfpr_graph* g = const_cast<dfpr_graph*>(gc);
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->stream;
+  DevArray<long long> toff;
+  DevArray<int32_t> tidx;
+  long long* doff = (long long*)offsets;
+  int32_t* didx = idx;
+  if (!on_device) {
+    toff.reset((size_t)g->n + 1, s);
+    tidx.reset((size_t)g->m + 1, s);
+    doff = toff.p;
+    didx = tidx.p;
+  }
+  graph_export(g, csr ? g->out : g->in, doff, didx);
+  if (!on_device) {
+    DFPR_CUDA(cudaMemcpyAsync(offsets, doff, sizeof(long long) * (g->n + 1), cudaMemcpyDeviceToHost, s));
+    DFPR_CUDA(cudaMemcpyAsync(idx, didx, sizeof(int32_t) * g->m, cudaMemcpyDeviceToHost, s));
+  }
+  DFPR_CUDA(cudaStreamSynchronize(s));
+  return DFPR_OK;
+  API_END
+}
+
+dfpr_status dfpr_get_csr(const dfpr_graph* g, int64_t* offsets, int32_t* idx, int on_device) {
+  return export_dir(g, true, offsets, idx, on_device);
+}
+
+dfpr_status dfpr_get_csc(const dfpr_graph* g, int64_t* offsets, int32_t* idx, int on_device) {
+  return export_dir(g, false, offsets, idx, on_device);
+}
+
+dfpr_status dfpr_initial_affected(dfpr_graph* g, uint8_t* affected, int on_device, int64_t* count) {
+  if (count) *count = 0;
+  if (!g || !affected) {
+    set_error("dfpr_initial_affected: NULL argument");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->stream;
+  DevArray<uint8_t> tmp;
+  uint8_t* dst = affected;
+  if (!on_device) {
+    tmp.reset((size_t)g->n, s);
+    dst = tmp.p;
+  }
+  long long c = 0;
+  initial_affected(g, dst, &c);
+  if (!on_device)
+    DFPR_CUDA(cudaMemcpyAsync(affected, dst, (size_t)g->n, cudaMemcpyDeviceToHost, s));
+  DFPR_CUDA(cudaStreamSynchronize(s));
+  if (count) *count = c;
+  return DFPR_OK;
+  API_END
+}
+
+}  // extern "C"

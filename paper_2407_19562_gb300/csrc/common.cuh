@@ -1,0 +1,185 @@
+// Internal definitions shared by the translation units of libdfpr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/dfpr.h"
+
+namespace dfpr {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+
+void set_error(const std::string& msg);
+const char* get_error();
+
+struct Fail {
+  dfpr_status st;
+};
+
+#define DFPR_CUDA(call)                                                          \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      ::dfpr::set_error(std::string(#call) + ": " + cudaGetErrorString(e_) +     \
+                        " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+      throw ::dfpr::Fail{DFPR_ECUDA};                                            \
+    }                                                                            \
+  } while (0)
+
+#define DFPR_REQUIRE(cond, code, msg)   \
+  do {                                  \
+    if (!(cond)) {                      \
+      ::dfpr::set_error(msg);           \
+      throw ::dfpr::Fail{code};         \
+    }                                   \
+  } while (0)
+
+// Kernel launches issued by the library (a process-wide counter).
+extern std::atomic<long long> g_launches;
+
+// Launch-error check after a kernel launch; also counts the launch.
+#define DFPR_LAUNCHED()                                   \
+  do {                                                    \
+    ::dfpr::g_launches.fetch_add(1, std::memory_order_relaxed); \
+    DFPR_CUDA(cudaGetLastError());                        \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device memory (through the installable allocator)
+// ---------------------------------------------------------------------------
+
+// The free routine that matches an allocation (captured when it was made).
+struct FreeRec {
+  dfpr_free_fn fn;
+  void* ctx;
+};
+void* dev_alloc(size_t bytes, cudaStream_t s, FreeRec* rec);  // throws Fail{ENOMEM}
+void dev_free(void* p, size_t bytes, cudaStream_t s, const FreeRec& rec);
+
+template <class T>
+struct DevArray {
+  T* p = nullptr;
+  size_t count = 0;
+  cudaStream_t s = nullptr;
+  FreeRec rec{nullptr, nullptr};
+  void reset(size_t n, cudaStream_t st) {
+    release();
+    s = st;
+    if (n) p = (T*)dev_alloc(n * sizeof(T), st, &rec);
+    count = n;
+  }
+  // Grows to at least n elements (contents are not preserved).
+  void ensure(size_t n, cudaStream_t st) {
+    if (n > count) reset(n + n / 4 + 64, st);
+  }
+  void release() {
+    if (p) dev_free(p, count * sizeof(T), s, rec);
+    p = nullptr;
+    count = 0;
+  }
+  DevArray() = default;
+  DevArray(const DevArray&) = delete;
+  DevArray& operator=(const DevArray&) = delete;
+  ~DevArray() { release(); }
+};
+
+// Scratch arena: numbered buffers that grow on demand (contents are not
+// preserved across growth). Slot numbers are assigned in graph.cu / df.cu /
+// primitives.cuh so that nested users never share a slot.
+struct Scratch {
+  DevArray<unsigned char> buf[40];
+  template <class T>
+  T* get(int slot, size_t n, cudaStream_t s) {
+    buf[slot].ensure(n * sizeof(T) + 16, s);
+    return (T*)buf[slot].p;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Graph layout
+// ---------------------------------------------------------------------------
+
+// One row of CSR or CSC: edges[off .. off + deg) hold the row, sorted; the
+// slot reserves cap >= deg entries so that batches update it in place.
+struct __align__(16) RowDesc {
+  long long off;
+  int deg;
+  int cap;
+};
+
+struct Rows {
+  DevArray<RowDesc> rows;          // n
+  DevArray<int32_t> edges;         // ecap
+  long long ecap = 0;              // capacity of edges
+  DevArray<unsigned long long> tail;  // 1: next free position of the spare area
+};
+
+// Device control block of one rank iteration (all counters 64-bit).
+struct DfCtl {
+  unsigned long long head;        // queue positions claimed by consumers
+  unsigned long long tail;        // queue positions claimed by producers
+  long long avail;                // pushed but not yet claimed
+  long long pending;              // queued + running vertices + open marking items
+  unsigned long long mark_next;   // next marking item to claim
+  unsigned long long n_src_items; // marking items over out-rows of sources
+  unsigned long long n_items;     // all marking items
+  unsigned int status;            // 0, or the dfpr_status that stopped the workers
+  unsigned int abort;             // 1: workers stop
+  unsigned long long processed, edges, expansions, edges_marked, pushes, affected;
+  unsigned long long max_change_bits;  // max |change| of a recomputation (bits of a double)
+  long long work_cap;             // cap on recomputations (worklist)
+  unsigned long long t_start;     // globaltimer at launch
+  long long len;                  // affected-list length (round / jacobi)
+  long long nc;                   // vertices flagged not converged (round)
+  double dsum;                    // rank held by dead ends (teleport)
+  unsigned long long pad[4];
+};
+
+struct Pending {
+  DevArray<int32_t> src;   // sources of real changes (marking: out-rows)
+  DevArray<int32_t> dst;   // targets of real deletions
+  long long n_src = 0, n_dst = 0;
+};
+
+}  // namespace dfpr
+
+struct dfpr_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int32_t n = 0;
+  int bits = 1;             // ids fit in `bits` bits
+  long long m = 0;          // live edges (both directions hold m)
+  long long last_real_del = 0;  // real deletions of the batch being applied
+  dfpr_graph_config cfg;
+  dfpr::Rows out, in;
+  // ranks: FP64 or FP32 arrays (one of each pair is used)
+  dfpr::DevArray<double> R64, C64, X64;   // rank, contribution R/outdeg, rank at last expansion
+  dfpr::DevArray<float> R32, C32, X32;
+  dfpr::DevArray<double> R64b, C64b;       // second vectors of the Jacobi schedule
+  dfpr::DevArray<float> R32b, C32b;
+  dfpr::DevArray<uint32_t> ep;            // epoch of first recomputation in the current call
+  uint32_t epoch = 0;
+  dfpr::DevArray<uint32_t> state;         // 2 bits per vertex: bit0 queued, bit1 running
+  dfpr::DevArray<int32_t> queue;          // qcap slots, -1 when empty
+  unsigned long long qcap = 0;
+  dfpr::DevArray<dfpr::DfCtl> ctl;
+  dfpr::DevArray<int32_t> affected_list;  // round mode: affected vertices in marking order
+  dfpr::DevArray<uint32_t> va_bits;       // round mode: affected bitmap
+  dfpr::DevArray<uint32_t> rc_bits;       // round mode: not-converged bitmap
+  dfpr::DevArray<unsigned long long> pass_ctr;  // round mode: per-pass claim counters
+  dfpr::DevArray<uint32_t> item_done;     // round mode: marking items completed (helping)
+  dfpr::Pending pend;
+  dfpr::Scratch scratch;
+  dfpr::DevArray<unsigned long long> host_sync;  // small device words read back
+  unsigned long long* pinned = nullptr;   // pinned host words for read-back
+  std::atomic<int> busy{0};
+  int sm_count = 0;
+  int max_ctas = 0;
+};

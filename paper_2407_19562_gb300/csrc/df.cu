@@ -1,0 +1,1400 @@
+// Rank iterations of the Dynamic Frontier approach (arXiv 2407.19562, Sec. 4)
+// and of the static / naive-dynamic baselines (Sec. 3.3, 3.5.1), on one GPU.
+//
+// Every schedule recomputes a vertex v with Eq. 1 as
+//     r = (1 - alpha) / n + alpha * sum_{u in in(v)} C[u],   C[u] = R[u] / |out(u)|
+// where C is kept next to R and refreshed whenever R[u] or |out(u)| changes,
+// so a gather reads one id and one value per in-edge.
+//
+// Schedules:
+//  * worklist (persistent kernel, no grid-wide barrier): vertices flagged
+//    not-converged sit in a device queue; a warp pops up to 32, recomputes
+//    them in place, marks out-neighbours when the rank has moved by more than
+//    the frontier tolerance since the vertex last marked them, and re-queues
+//    itself while its change exceeds the iteration tolerance. Each vertex has
+//    a 2-bit state (queued, running) so that no vertex is recomputed by two
+//    warps at once and no update is lost. The iteration ends when the count
+//    of queued + running vertices + open marking items reaches zero.
+//  * round (Alg. 2): every affected vertex is recomputed in every pass; warps
+//    claim chunks of a pass from a per-pass counter and move to the next pass
+//    without waiting; a per-vertex not-converged flag R_C and its count end
+//    the iteration; marking uses the helping rule (unfinished marking items
+//    are redone by idle warps).
+//  * jacobi (Alg. 1 / Alg. 3 / Alg. 5): two vectors, one kernel per iteration,
+//    L-inf reduction, swap; marks take effect from the next iteration.
+//
+// Every wait is bounded by the call's time budget (%globaltimer); on expiry
+// the kernel records DFPR_ETIMEOUT and returns.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "df.cuh"
+#include "graph.cuh"
+#include "primitives.cuh"
+
+namespace dfpr {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNT = 256;
+constexpr int kWPB = kNT / 32;
+constexpr int kMarkChunk = 1024;  // out-edges per marking item
+
+// Scratch slots (see common.cuh; graph.cu uses 0..28).
+enum { kSMarkCnt = 30, kSMarkOff = 31 };
+
+#define GRID_STRIDE(i, n)                                                             \
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
+       i += (long long)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ long long ld_volatile(const long long* p) {
+  return *(const volatile long long*)p;
+}
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *(const volatile unsigned*)p;
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+__device__ __forceinline__ void atomic_add_ll(long long* p, long long v) {
+  atomicAdd((unsigned long long*)p, (unsigned long long)v);
+}
+__device__ __forceinline__ long long atomic_add_ll_old(long long* p, long long v) {
+  return (long long)atomicAdd((unsigned long long*)p, (unsigned long long)v);
+}
+
+// ---------------------------------------------------------------------------
+// Precision traits
+// ---------------------------------------------------------------------------
+
+// FP64: plain sums.
+struct P64 {
+  using val = double;
+  using acc = double;
+  static __device__ __forceinline__ acc zero() { return 0.0; }
+  static __device__ __forceinline__ acc from(val x) { return x; }
+  static __device__ __forceinline__ acc add(acc a, acc b) { return a + b; }
+  static __device__ __forceinline__ double total(acc a) { return a; }
+  static __device__ __forceinline__ acc shfl_up(acc a, int d) { return __shfl_up_sync(kFull, a, d); }
+  static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
+  static constexpr bool relative = false;
+};
+
+// FP32 with compensated summation: every addition is an error-free TwoSum
+// (Knuth); the rounding errors are carried in a second float.
+struct CompF {
+  float s, c;
+};
+struct P32 {
+  using val = float;
+  using acc = CompF;
+  static __device__ __forceinline__ acc zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ acc from(val x) { return {x, 0.f}; }
+  static __device__ __forceinline__ acc add(acc a, acc b) {
+    const float s = __fadd_rn(a.s, b.s);
+    const float bp = __fsub_rn(s, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bp)), __fsub_rn(b.s, bp));
+    return {s, __fadd_rn(__fadd_rn(a.c, b.c), err)};
+  }
+  static __device__ __forceinline__ double total(acc a) { return (double)a.s + (double)a.c; }
+  static __device__ __forceinline__ acc shfl_up(acc a, int d) {
+    return {__shfl_up_sync(kFull, a.s, d), __shfl_up_sync(kFull, a.c, d)};
+  }
+  static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
+  static constexpr bool relative = true;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel arguments
+// ---------------------------------------------------------------------------
+
+template <class P>
+struct Args {
+  int32_t n;
+  const RowDesc* __restrict__ in_rows;
+  const int32_t* __restrict__ in_edges;
+  const RowDesc* __restrict__ out_rows;
+  const int32_t* __restrict__ out_edges;
+  typename P::val* R;
+  typename P::val* C;
+  typename P::val* X;
+  uint32_t* ep;
+  uint32_t epoch;
+  uint32_t* state;
+  int32_t* queue;
+  unsigned long long qmask;
+  DfCtl* ctl;
+  // marking items
+  const int32_t* mark_src;
+  const long long* mark_choff;  // exclusive scan of marking chunks per source
+  long long n_mark_src;
+  const int32_t* mark_dst;
+  long long n_mark_dst;
+  // round mode
+  uint32_t* va_bits;
+  uint32_t* rc_bits;
+  int32_t* alist;
+  unsigned long long* pass_ctr;
+  uint32_t* item_done;
+  int max_iter;
+  // numerics
+  double alpha, base, tol, tol_f;
+  int teleport;
+  unsigned long long timeout_ns;
+  int mark_only;
+};
+
+struct WarpStats {
+  unsigned long long edges, expansions, edges_marked, pushes, affected;
+  double max_change;
+};
+
+template <class P>
+__device__ __forceinline__ bool timed_out(const Args<P>& a) {
+  return gtime() - a.ctl->t_start > a.timeout_ns;
+}
+
+template <class P>
+__device__ void stop_with(const Args<P>& a, unsigned status) {
+  atomicCAS(&a.ctl->status, 0u, status);
+  atomicExch(&a.ctl->abort, 1u);
+}
+
+// Warp-cooperative edge-balanced gather: lane i owns vertex v_i (or -1).
+// Returns sum_{u in in(v_i)} C[u] in lane i.
+template <class P>
+__device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl, long long* s_off,
+                                  typename P::acc* s_acc, WarpStats& st) {
+  int deg = 0;
+  long long off = 0;
+  if (v >= 0) {
+    const RowDesc r = a.in_rows[v];
+    deg = r.deg;
+    off = r.off;
+  }
+  int incl = deg;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  s_excl[lane] = incl - deg;
+  s_off[lane] = off;
+  s_acc[lane] = P::zero();
+  __syncwarp();
+  for (int base = 0; base < total; base += 32) {
+    const int e = base + lane;
+    const bool valid = e < total;
+    int owner = 0;
+    typename P::acc x = P::zero();
+    if (valid) {
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_excl[mid] <= e) lo = mid; else hi = mid;
+      }
+      owner = lo;
+      const int u = a.in_edges[s_off[owner] + (e - s_excl[owner])];
+      x = P::from(P::load(a.C + u));
+    }
+    const int key = valid ? owner : 32 + lane;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const typename P::acc y = P::shfl_up(x, d);
+      const int k2 = __shfl_up_sync(kFull, key, d);
+      if (lane >= d && k2 == key) x = P::add(x, y);
+    }
+    const int knext = __shfl_down_sync(kFull, key, 1);
+    if (valid && (lane == 31 || knext != key)) s_acc[owner] = P::add(s_acc[owner], x);
+    __syncwarp();
+  }
+  st.edges += (unsigned long long)deg;
+  return s_acc[lane];
+}
+
+// Pushes t for every lane with need (warp-uniform call). Lane 0 performs all
+// counter updates of the warp, so that pending increments precede this warp's
+// later decrements in program order.
+template <class P>
+__device__ bool push_warp(const Args<P>& a, int t, bool need, bool count_pending, int lane,
+                          WarpStats& st) {
+  const unsigned b = __ballot_sync(kFull, need);
+  if (!b) return true;
+  const int cnt = __popc(b);
+  unsigned long long base = 0;
+  if (lane == 0) {
+    if (count_pending) atomic_add_ll(&a.ctl->pending, cnt);
+    base = atomicAdd(&a.ctl->tail, (unsigned long long)cnt);
+    st.pushes += cnt;
+  }
+  base = __shfl_sync(kFull, base, 0);
+  bool ok = true;
+  if (need) {
+    const unsigned long long pos = base + __popc(b & lanemask_lt());
+    int* slot = a.queue + (pos & a.qmask);
+    unsigned spins = 0;
+    while (ld_volatile(slot) != -1) {  // slot still held by a slow consumer
+      if ((++spins & 255u) == 0 && timed_out(a)) {
+        stop_with(a, DFPR_ETIMEOUT);
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (ok) *(volatile int*)slot = t;
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomic_add_ll(&a.ctl->avail, cnt);
+  return __all_sync(kFull, ok);
+}
+
+// Sets the queued bit of t (lanes with valid) and pushes vertices that were idle.
+template <class P>
+__device__ void mark_push(const Args<P>& a, int t, bool valid, int lane, WarpStats& st) {
+  bool need = false;
+  if (valid) {
+    const unsigned sh = (unsigned)(t & 15) * 2u;
+    const unsigned old = atomicOr(a.state + (t >> 4), 1u << sh);
+    need = ((old >> sh) & 3u) == 0u;
+  }
+  push_warp(a, t, need, true, lane, st);
+}
+
+// Marking item: a chunk of a source's out-row, or up to 32 deletion targets.
+// For the DF approach (Sec. 4.1) the affected set is out_{t-1}(u) union
+// out_t(u) = out_t(u) plus the targets of u's deleted edges.
+template <class P, class MarkFn>
+__device__ void do_mark_item(const Args<P>& a, long long item, int lane, WarpStats& st, MarkFn mark) {
+  const long long n_src_items = (long long)a.ctl->n_src_items;
+  if (item < n_src_items) {
+    long long lo = 0, hi = a.n_mark_src;  // last s with choff[s] <= item
+    while (hi - lo > 1) {
+      const long long mid = (lo + hi) >> 1;
+      if (a.mark_choff[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int u = a.mark_src[lo];
+    const long long chunk = item - a.mark_choff[lo];
+    const RowDesc r = a.out_rows[u];
+    const long long beg = chunk * kMarkChunk;
+    const long long end = min((long long)r.deg, beg + kMarkChunk);
+    for (long long e0 = beg; e0 < end; e0 += 32) {
+      const long long e = e0 + lane;
+      const bool valid = e < end;
+      const int t = valid ? a.out_edges[r.off + e] : 0;
+      mark(t, valid);
+    }
+    if (lane == 0) st.edges_marked += (unsigned long long)max(0ll, end - beg);
+  } else {
+    const long long j = (item - n_src_items) * 32 + lane;
+    const bool valid = j < a.n_mark_dst;
+    const int t = valid ? a.mark_dst[j] : 0;
+    mark(t, valid);
+    if (lane == 0) st.edges_marked += (unsigned long long)min(32ll, a.n_mark_dst - (item - n_src_items) * 32);
+  }
+}
+
+template <class P>
+__device__ void flush_stats(const Args<P>& a, WarpStats& st, int lane) {
+  // every lane holds partial counts; reduce to lane 0
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    st.edges += __shfl_down_sync(kFull, st.edges, d);
+    st.expansions += __shfl_down_sync(kFull, st.expansions, d);
+    st.affected += __shfl_down_sync(kFull, st.affected, d);
+    st.max_change = fmax(st.max_change, __shfl_down_sync(kFull, st.max_change, d));
+  }
+  if (lane == 0) {
+    DfCtl* c = a.ctl;
+    if (st.edges) atomicAdd(&c->edges, st.edges);
+    if (st.expansions) atomicAdd(&c->expansions, st.expansions);
+    if (st.edges_marked) atomicAdd(&c->edges_marked, st.edges_marked);
+    if (st.pushes) atomicAdd(&c->pushes, st.pushes);
+    if (st.affected) atomicAdd(&c->affected, st.affected);
+    if (st.max_change > 0) atomicMax(&c->max_change_bits, (unsigned long long)__double_as_longlong(st.max_change));
+  }
+}
+
+// Eq. 1 for a recomputed vertex, from its gathered sum.
+template <class P>
+__device__ __forceinline__ typename P::val finish_rank(const Args<P>& a, typename P::acc acc,
+                                                       double dangling) {
+  double s = P::total(acc);
+  if (a.teleport) s += dangling / (double)a.n;
+  return (typename P::val)(a.base + a.alpha * s);
+}
+
+// ---------------------------------------------------------------------------
+// Worklist schedule
+// ---------------------------------------------------------------------------
+
+template <class P>
+__global__ void __launch_bounds__(kNT) k_worklist(Args<P> a) {
+  __shared__ int s_excl[kWPB][32];
+  __shared__ long long s_off[kWPB][32];
+  __shared__ typename P::acc s_acc[kWPB][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  DfCtl* ctl = a.ctl;
+  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  auto mark = [&](int t, bool valid) { mark_push(a, t, valid, lane, st); };
+
+  // Stage 1: initial marking. Each item holds one unit of `pending` until its
+  // pushes are done, so the iteration cannot end while marking is open.
+  const unsigned long long n_items = ctl->n_items;
+  while (true) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(&ctl->mark_next, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= n_items) break;
+    do_mark_item(a, (long long)item, lane, st, mark);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomic_add_ll(&ctl->pending, -1);
+    }
+  }
+
+  // Stage 2: recompute queued vertices until nothing is queued or running.
+  unsigned backoff = 32;
+  while (!a.mark_only) {
+    // claim up to 32 items
+    long long got = 0;
+    unsigned long long h = 0;
+    if (lane == 0) {
+      if (ld_volatile(&ctl->avail) > 0) {
+        const long long av = atomic_add_ll_old(&ctl->avail, -32);
+        got = av >= 32 ? 32 : (av > 0 ? av : 0);
+        if (got < 32) atomic_add_ll(&ctl->avail, 32 - got);
+        if (got) h = atomicAdd(&ctl->head, (unsigned long long)got);
+      }
+    }
+    got = __shfl_sync(kFull, got, 0);
+    if (got == 0) {
+      int stop = 0;
+      if (lane == 0) {
+        if (ld_volatile(&ctl->abort) || ld_volatile(&ctl->pending) <= 0) stop = 1;
+        else if (timed_out(a)) {
+          stop_with(a, DFPR_ETIMEOUT);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(kFull, stop, 0)) break;
+      __nanosleep(backoff);
+      backoff = min(backoff * 2, 2048u);
+      continue;
+    }
+    backoff = 32;
+    h = __shfl_sync(kFull, h, 0);
+    int v = -1;
+    bool ok = true;
+    if (lane < got) {
+      int* slot = a.queue + ((h + lane) & a.qmask);
+      unsigned spins = 0;
+      while ((v = ld_volatile(slot)) < 0) {  // producer between claim and write
+        if ((++spins & 255u) == 0 && timed_out(a)) {
+          stop_with(a, DFPR_ETIMEOUT);
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (ok) {
+        *(volatile int*)slot = -1;
+        const unsigned sh = (unsigned)(v & 15) * 2u;
+        atomicXor(a.state + (v >> 4), 3u << sh);  // queued -> running
+      } else {
+        v = -1;
+      }
+    }
+    if (!__all_sync(kFull, ok)) break;
+    __threadfence();  // state change before reading neighbours' contributions
+
+    const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
+    const double dangling = a.teleport ? ctl->dsum : 0.0;
+    bool expand = false, requeue = false;
+    if (v >= 0) {
+      const typename P::val r = finish_rank(a, acc, dangling);
+      const typename P::val r_old = P::load(a.R + v);
+      const uint32_t e = __ldcg(a.ep + v);
+      typename P::val x0;
+      if (e != a.epoch) {
+        a.ep[v] = a.epoch;
+        x0 = r_old;
+        st.affected++;
+      } else {
+        x0 = P::load(a.X + v);
+      }
+      const double dr = fabs((double)r - (double)r_old);
+      const int od = a.out_rows[v].deg;
+      a.R[v] = r;
+      a.C[v] = od > 0 ? r / (typename P::val)od : (typename P::val)0;
+      const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
+      const double thr = P::relative ? a.tol * fabs((double)r) : a.tol;
+      expand = fabs((double)r - (double)x0) > thr_f;
+      a.X[v] = expand ? r : x0;
+      requeue = dr > thr;
+      st.max_change = fmax(st.max_change, dr);
+      if (expand) st.expansions++;
+    }
+    __threadfence();  // new rank visible before neighbours are queued
+
+    // Expansion: mark the out-neighbours of every expanding vertex.
+    {
+      int od = 0;
+      long long oo = 0;
+      if (expand) {
+        const RowDesc r = a.out_rows[v];
+        od = r.deg;
+        oo = r.off;
+      }
+      int incl = od;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      __syncwarp();
+      s_excl[w][lane] = incl - od;
+      s_off[w][lane] = oo;
+      __syncwarp();
+      for (int base = 0; base < total; base += 32) {
+        const int e = base + lane;
+        const bool valid = e < total;
+        int t = 0;
+        if (valid) {
+          int lo = 0, hi = 32;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_excl[w][mid] <= e) lo = mid; else hi = mid;
+          }
+          t = a.out_edges[s_off[w][lo] + (e - s_excl[w][lo])];
+        }
+        mark_push(a, t, valid, lane, st);
+      }
+      if (lane == 0) st.edges_marked += (unsigned long long)total;
+    }
+    // Not converged: flag itself so that the finish step re-queues it.
+    if (requeue && !expand) {
+      const unsigned sh = (unsigned)(v & 15) * 2u;
+      atomicOr(a.state + (v >> 4), 1u << sh);
+    }
+    // Finish: running -> idle, or -> queued (re-pushed) when flagged meanwhile.
+    bool repush = false;
+    if (v >= 0) {
+      const unsigned sh = (unsigned)(v & 15) * 2u;
+      const unsigned old = atomicAnd(a.state + (v >> 4), ~(2u << sh));
+      repush = ((old >> sh) & 1u) != 0u;
+    }
+    push_warp(a, v, repush, false, lane, st);
+    const int done = __popc(__ballot_sync(kFull, v >= 0 && !repush));
+    if (lane == 0) {
+      __threadfence();
+      if (done) atomic_add_ll(&ctl->pending, -done);
+      const unsigned long long pr = atomicAdd(&ctl->processed, (unsigned long long)got);
+      if ((long long)(pr + got) > ctl->work_cap) stop_with(a, DFPR_ENOTCONV);
+    }
+  }
+  flush_stats(a, st, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Round schedule (Alg. 2)
+// ---------------------------------------------------------------------------
+
+// Marks t affected (appending it to the affected list once) and not converged.
+template <class P>
+__device__ void mark_round(const Args<P>& a, int t, bool valid, int lane) {
+  bool fresh = false;
+  long long nc_add = 0;
+  if (valid) {
+    const uint32_t bit = 1u << (t & 31);
+    fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
+    nc_add = (atomicOr(a.rc_bits + (t >> 5), bit) & bit) == 0u ? 1 : 0;
+  }
+  const unsigned b = __ballot_sync(kFull, fresh);
+  const unsigned nb = __ballot_sync(kFull, nc_add != 0);
+  long long base = 0;
+  if (lane == 0) {
+    if (nb) atomic_add_ll(&a.ctl->nc, __popc(nb));
+    if (b) base = atomic_add_ll_old(&a.ctl->len, __popc(b));
+  }
+  base = __shfl_sync(kFull, base, 0);
+  if (fresh) *(volatile int*)(a.alist + base + __popc(b & lanemask_lt())) = t;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
+  __shared__ int s_excl[kWPB][32];
+  __shared__ long long s_off[kWPB][32];
+  __shared__ typename P::acc s_acc[kWPB][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  DfCtl* ctl = a.ctl;
+  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  auto mark = [&](int t, bool valid) { mark_round(a, t, valid, lane); };
+
+  // Marking phase with helping (Alg. 2 marking loop): claim items; then, until
+  // every item is done, redo items that are still open (idempotent).
+  const unsigned long long n_items = ctl->n_items;
+  while (true) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(&ctl->mark_next, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= n_items) break;
+    do_mark_item(a, (long long)item, lane, st, mark);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      if (atomicExch(a.item_done + item, 1u) == 0u) atomic_add_ll(&ctl->pending, -1);
+    }
+  }
+  {
+    unsigned long long scan = (unsigned long long)(blockIdx.x * kWPB + w);
+    const unsigned long long stride = (unsigned long long)gridDim.x * kWPB;
+    unsigned spins = 0;
+    while (true) {
+      int stop = 0;
+      if (lane == 0) {
+        if (ld_volatile(&ctl->pending) <= 0 || ld_volatile(&ctl->abort)) stop = 1;
+        else if ((++spins & 63u) == 0 && timed_out(a)) {
+          stop_with(a, DFPR_ETIMEOUT);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(kFull, stop, 0)) break;
+      const unsigned long long item = scan % n_items;
+      scan += stride;
+      if (ld_volatile(a.item_done + item) == 0u) {  // help an unfinished item
+        do_mark_item(a, (long long)item, lane, st, mark);
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          if (atomicExch(a.item_done + item, 1u) == 0u) atomic_add_ll(&ctl->pending, -1);
+        }
+      }
+    }
+  }
+  if (a.mark_only || ld_volatile(&ctl->abort)) {
+    flush_stats(a, st, lane);
+    return;
+  }
+
+  // Passes (Alg. 2 iteration loop).
+  int pass = 0;
+  for (; pass < a.max_iter; ++pass) {
+    while (true) {
+      unsigned long long c = 0;
+      long long len = 0;
+      if (lane == 0) {
+        c = atomicAdd(a.pass_ctr + pass, 32ull);
+        len = ld_volatile(&ctl->len);
+      }
+      c = __shfl_sync(kFull, c, 0);
+      len = __shfl_sync(kFull, len, 0);
+      if ((long long)c >= len) break;
+      const long long j = (long long)c + lane;
+      int v = -1;
+      bool ok = true;
+      if (j < len) {
+        unsigned spins = 0;
+        while ((v = ld_volatile(a.alist + j)) < 0) {  // appended but not yet written
+          if ((++spins & 255u) == 0 && timed_out(a)) {
+            stop_with(a, DFPR_ETIMEOUT);
+            ok = false;
+            break;
+          }
+          __nanosleep(32);
+        }
+        if (!ok) v = -1;
+      }
+      if (!__all_sync(kFull, ok)) break;
+      const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
+      bool expand = false;
+      double dr = 0.0, thr = 0.0;
+      if (v >= 0) {
+        const typename P::val r = finish_rank(a, acc, 0.0);
+        const typename P::val r_old = P::load(a.R + v);
+        dr = fabs((double)r - (double)r_old);
+        const int od = a.out_rows[v].deg;
+        a.R[v] = r;
+        a.C[v] = od > 0 ? r / (typename P::val)od : (typename P::val)0;
+        const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
+        thr = P::relative ? a.tol * fabs((double)r) : a.tol;
+        expand = dr > thr_f;
+        st.max_change = fmax(st.max_change, dr);
+        if (expand) st.expansions++;
+      }
+      // expansion first (with self-loops it flags v itself), then v's own flag
+      {
+        int od = 0;
+        long long oo = 0;
+        if (expand) {
+          const RowDesc r = a.out_rows[v];
+          od = r.deg;
+          oo = r.off;
+        }
+        int incl = od;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          int y = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        __syncwarp();
+        s_excl[w][lane] = incl - od;
+        s_off[w][lane] = oo;
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+          const int e = base + lane;
+          const bool valid = e < total;
+          int t = 0;
+          if (valid) {
+            int lo = 0, hi = 32;
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (s_excl[w][mid] <= e) lo = mid; else hi = mid;
+            }
+            t = a.out_edges[s_off[w][lo] + (e - s_excl[w][lo])];
+          }
+          mark_round(a, t, valid, lane);
+        }
+        if (lane == 0) st.edges_marked += (unsigned long long)total;
+      }
+      long long conv = 0;
+      if (v >= 0) {
+        if (dr <= thr) {
+          const uint32_t bit = 1u << (v & 31);
+          if (atomicAnd(a.rc_bits + (v >> 5), ~bit) & bit) conv = 1;
+        }
+      }
+      const unsigned cb = __ballot_sync(kFull, conv != 0);
+      if (lane == 0) {
+        if (cb) atomic_add_ll(&ctl->nc, -(long long)__popc(cb));
+        const int cnt = (int)min(32ll, len - (long long)c);
+        atomicAdd(&ctl->processed, (unsigned long long)cnt);
+      }
+    }
+    int stop = 0;
+    if (lane == 0) {
+      if (ld_volatile(&ctl->nc) <= 0 || ld_volatile(&ctl->abort)) stop = 1;
+      else if (timed_out(a)) {
+        stop_with(a, DFPR_ETIMEOUT);
+        stop = 1;
+      }
+    }
+    if (__shfl_sync(kFull, stop, 0)) {
+      ++pass;
+      break;
+    }
+  }
+  if (lane == 0) atomicMax((unsigned long long*)&ctl->pad[0], (unsigned long long)pass);
+  flush_stats(a, st, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi schedule: one iteration over a vertex list (or all vertices)
+// ---------------------------------------------------------------------------
+
+template <class P>
+__global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val* __restrict__ Rin,
+                                                const typename P::val* __restrict__ Cin,
+                                                typename P::val* __restrict__ Rout,
+                                                typename P::val* __restrict__ Cout,
+                                                const int32_t* __restrict__ list, long long count,
+                                                int frontier) {
+  __shared__ int s_excl[kWPB][32];
+  __shared__ long long s_off[kWPB][32];
+  __shared__ typename P::acc s_acc[kWPB][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  Args<P> b = a;
+  b.C = const_cast<typename P::val*>(Cin);
+  const long long nbatch = (count + 31) / 32;
+  const double dangling = a.teleport ? a.ctl->dsum : 0.0;
+  for (long long bi = (long long)blockIdx.x * kWPB + w; bi < nbatch; bi += (long long)gridDim.x * kWPB) {
+    const long long j = bi * 32 + lane;
+    const int v = j < count ? (list ? list[j] : (int)j) : -1;
+    const typename P::acc acc = gather(b, v, lane, s_excl[w], s_off[w], s_acc[w], st);
+    bool expand = false;
+    if (v >= 0) {
+      const typename P::val r = finish_rank(b, acc, dangling);
+      const double dr = fabs((double)r - (double)Rin[v]);
+      const int od = a.out_rows[v].deg;
+      Rout[v] = r;
+      Cout[v] = od > 0 ? r / (typename P::val)od : (typename P::val)0;
+      const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
+      expand = frontier && dr > thr_f;
+      st.max_change = fmax(st.max_change, dr);
+      if (expand) st.expansions++;
+    }
+    if (frontier) {
+      int od = 0;
+      long long oo = 0;
+      if (expand) {
+        const RowDesc r = a.out_rows[v];
+        od = r.deg;
+        oo = r.off;
+      }
+      int incl = od;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      __syncwarp();
+      s_excl[w][lane] = incl - od;
+      s_off[w][lane] = oo;
+      __syncwarp();
+      for (int base = 0; base < total; base += 32) {
+        const int e = base + lane;
+        const bool valid = e < total;
+        int t = 0;
+        if (valid) {
+          int lo = 0, hi = 32;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_excl[w][mid] <= e) lo = mid; else hi = mid;
+          }
+          t = a.out_edges[s_off[w][lo] + (e - s_excl[w][lo])];
+        }
+        // affected from the next iteration on: the list grows past `count`
+        bool fresh = false;
+        if (valid) {
+          const uint32_t bit = 1u << (t & 31);
+          fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
+        }
+        const unsigned bb = __ballot_sync(kFull, fresh);
+        long long base2 = 0;
+        if (lane == 0 && bb) base2 = atomic_add_ll_old(&a.ctl->len, __popc(bb));
+        base2 = __shfl_sync(kFull, base2, 0);
+        if (fresh) a.alist[base2 + __popc(bb & lanemask_lt())] = t;
+      }
+      if (lane == 0) st.edges_marked += (unsigned long long)total;
+    }
+    if (lane == 0) atomicAdd(&a.ctl->processed, (unsigned long long)min(32ll, count - bi * 32));
+  }
+  flush_stats(a, st, lane);
+}
+
+// Initial marking for the Jacobi schedule: affected list + bitmap.
+template <class P>
+__global__ void __launch_bounds__(kNT) k_mark_list(Args<P> a) {
+  const int lane = threadIdx.x & 31;
+  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  auto mark = [&](int t, bool valid) {
+    bool fresh = false;
+    if (valid) {
+      const uint32_t bit = 1u << (t & 31);
+      fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
+    }
+    const unsigned b = __ballot_sync(kFull, fresh);
+    long long base = 0;
+    if (lane == 0 && b) base = atomic_add_ll_old(&a.ctl->len, __popc(b));
+    base = __shfl_sync(kFull, base, 0);
+    if (fresh) a.alist[base + __popc(b & lanemask_lt())] = t;
+  };
+  const unsigned long long n_items = a.ctl->n_items;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long item = warp; item < (long long)n_items; item += nw) do_mark_item(a, item, lane, st, mark);
+  flush_stats(a, st, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Small helper kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_mark_chunks(const int32_t* __restrict__ src, long long ns,
+                              const RowDesc* __restrict__ out_rows, long long* cnt) {
+  GRID_STRIDE(i, ns) {
+    const long long d = out_rows[src[i]].deg;
+    cnt[i] = d > 0 ? (d + kMarkChunk - 1) / kMarkChunk : 1;
+  }
+}
+
+__global__ void k_init_ctl(DfCtl* c, const long long* n_src_items_dev, long long n_mark_dst,
+                           long long work_cap, long long seeded, int count_items_pending) {
+  const unsigned long long nsi = n_src_items_dev ? (unsigned long long)*n_src_items_dev : 0ull;
+  const unsigned long long items = nsi + (unsigned long long)((n_mark_dst + 31) / 32);
+  DfCtl z;
+  memset(&z, 0, sizeof z);
+  z.n_src_items = nsi;
+  z.n_items = items;
+  z.pending = (count_items_pending ? (long long)items : 0) + seeded;
+  z.tail = (unsigned long long)seeded;
+  z.avail = seeded;
+  z.work_cap = work_cap;
+  z.len = 0;
+  z.t_start = gtime();
+  *c = z;
+}
+
+__global__ void k_seed_all(int32_t n, uint32_t* state, int32_t* queue) {
+  GRID_STRIDE(i, n) {
+    queue[i] = (int32_t)i;
+    if ((i & 15) == 0) {
+      const long long rem = n - i;
+      state[i >> 4] = rem >= 16 ? 0x55555555u : (uint32_t)((1ull << (2 * rem)) - 1) & 0x55555555u;
+    }
+  }
+}
+
+template <class T>
+__global__ void k_fill(T* p, long long n, T v) {
+  GRID_STRIDE(i, n) p[i] = v;
+}
+
+template <class T>
+__global__ void k_init_ranks(int32_t n, const RowDesc* __restrict__ out_rows, T* R, T* C) {
+  const T r0 = (T)(1.0 / (double)n);
+  GRID_STRIDE(u, n) {
+    R[u] = r0;
+    const int d = out_rows[u].deg;
+    C[u] = d > 0 ? r0 / (T)d : (T)0;
+  }
+}
+
+__global__ void k_export_state(int32_t n, const uint32_t* __restrict__ state, uint8_t* out) {
+  GRID_STRIDE(v, n) out[v] = ((state[v >> 4] >> ((v & 15) * 2)) & 3u) ? 1 : 0;
+}
+
+
+// Clears the affected / not-converged bits of the listed vertices and the list.
+__global__ void k_clear_list(int32_t* alist, long long len, uint32_t* va, uint32_t* rc) {
+  GRID_STRIDE(i, len) {
+    const int v = alist[i];
+    if (v >= 0) {
+      const uint32_t bit = 1u << (v & 31);
+      if (va) atomicAnd(va + (v >> 5), ~bit);
+      if (rc) atomicAnd(rc + (v >> 5), ~bit);
+    }
+    alist[i] = -1;
+  }
+}
+
+template <class T>
+__global__ void k_sum_ranks(int32_t n, const T* __restrict__ R, double* out) {
+  __shared__ double sh[kWPB];
+  double s = 0.0;
+  GRID_STRIDE(i, n) s += (double)R[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(kFull, s, d);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kWPB; ++i) t += sh[i];
+    atomicAdd(out, t);
+  }
+}
+
+template <class T>
+__global__ void k_dangling(int32_t n, const RowDesc* __restrict__ out_rows, const T* __restrict__ R,
+                           double* out) {
+  __shared__ double sh[kWPB];
+  double s = 0.0;
+  GRID_STRIDE(i, n) if (out_rows[i].deg == 0) s += (double)R[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(kFull, s, d);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kWPB; ++i) t += sh[i];
+    atomicAdd(out, t);
+  }
+}
+
+template <class T>
+__global__ void k_scale(int32_t n, const RowDesc* __restrict__ out_rows, T* R, T* C, const double* sum) {
+  const double inv = 1.0 / *sum;
+  GRID_STRIDE(u, n) {
+    const T r = (T)((double)R[u] * inv);
+    R[u] = r;
+    const int d = out_rows[u].deg;
+    C[u] = d > 0 ? r / (T)d : (T)0;
+  }
+}
+
+// ND / static round schedule: the affected list is every vertex.
+__global__ void k_seed_round(int32_t n, int32_t* alist, DfCtl* c) {
+  GRID_STRIDE(i, n) alist[i] = (int32_t)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->len = n;
+    c->nc = n;
+  }
+}
+
+unsigned grid_small(long long n) { return blocks_for(n, kNT, 152u * 16u); }
+
+// ---------------------------------------------------------------------------
+// Host drivers
+// ---------------------------------------------------------------------------
+
+template <class P>
+Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
+  Args<P> a;
+  memset(&a, 0, sizeof a);
+  a.n = g->n;
+  a.in_rows = g->in.rows.p;
+  a.in_edges = g->in.edges.p;
+  a.out_rows = g->out.rows.p;
+  a.out_edges = g->out.edges.p;
+  a.ep = g->ep.p;
+  a.epoch = g->epoch;
+  a.state = g->state.p;
+  a.queue = g->queue.p;
+  a.qmask = g->qcap - 1;
+  a.ctl = g->ctl.p;
+  a.va_bits = g->va_bits.p;
+  a.rc_bits = g->rc_bits.p;
+  a.alist = g->affected_list.p;
+  a.pass_ctr = g->pass_ctr.p;
+  a.item_done = g->item_done.p;
+  a.max_iter = p.max_iter;
+  a.alpha = p.alpha;
+  a.base = (1.0 - p.alpha) / (double)g->n;
+  a.tol = p.tol;
+  a.tol_f = p.frontier_tol > 0 ? p.frontier_tol : p.tol / 1000.0;
+  a.teleport = g->cfg.dead_end == DFPR_TELEPORT;
+  const double tmo = p.timeout_ms > 0 ? p.timeout_ms : 60000.0;
+  a.timeout_ns = (unsigned long long)(tmo * 1e6);
+  return a;
+}
+
+template <class P>
+void set_vectors(dfpr_graph* g, Args<P>& a);
+template <>
+void set_vectors<P64>(dfpr_graph* g, Args<P64>& a) {
+  a.R = g->R64.p;
+  a.C = g->C64.p;
+  a.X = g->X64.p;
+}
+template <>
+void set_vectors<P32>(dfpr_graph* g, Args<P32>& a) {
+  a.R = g->R32.p;
+  a.C = g->C32.p;
+  a.X = g->X32.p;
+}
+
+int persistent_grid(dfpr_graph* g, const dfpr_params& p, const void* kernel) {
+  if (p.grid_ctas > 0) return p.grid_ctas;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kNT, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * g->sm_count;
+}
+
+// Prepares marking items for the pending change set; returns the device
+// pointer holding the number of source items.
+template <class P>
+long long* prepare_marking(dfpr_graph* g, Args<P>& a) {
+  cudaStream_t s = g->stream;
+  const long long ns = g->pend.n_src;
+  long long* cnt = g->scratch.get<long long>(kSMarkCnt, (size_t)ns + 1, s);
+  long long* off = g->scratch.get<long long>(kSMarkOff, (size_t)ns + 1, s);
+  if (ns > 0) {
+    k_mark_chunks<<<grid_small(ns), kNT, 0, s>>>(g->pend.src.p, ns, g->out.rows.p, cnt);
+    DFPR_LAUNCHED();
+  }
+  scan_exclusive_i64(cnt, off, ns, off + ns, g->scratch, s);
+  a.mark_src = g->pend.src.p;
+  a.mark_choff = off;
+  a.n_mark_src = ns;
+  a.mark_dst = g->pend.dst.p;
+  a.n_mark_dst = g->pend.n_dst;
+  return off + ns;
+}
+
+struct CtlHost {
+  DfCtl c;
+};
+
+CtlHost read_ctl(dfpr_graph* g) {
+  CtlHost h;
+  DFPR_CUDA(cudaMemcpyAsync(&h.c, g->ctl.p, sizeof(DfCtl), cudaMemcpyDeviceToHost, g->stream));
+  DFPR_CUDA(cudaStreamSynchronize(g->stream));
+  return h;
+}
+
+void fill_stats(const DfCtl& c, dfpr_stats* st) {
+  st->processed = (int64_t)c.processed;
+  st->edges_gathered = (int64_t)c.edges;
+  st->expansions = (int64_t)c.expansions;
+  st->edges_marked = (int64_t)c.edges_marked;
+  st->pushes = (int64_t)c.pushes;
+  st->affected = (int64_t)c.affected;
+  double mc;
+  memcpy(&mc, &c.max_change_bits, sizeof mc);
+  st->residual_linf = mc;
+}
+
+// Resets the queue and states after an aborted worklist run.
+void reset_worklist_state(dfpr_graph* g) {
+  cudaStream_t s = g->stream;
+  DFPR_CUDA(cudaMemsetAsync(g->state.p, 0, sizeof(uint32_t) * g->state.count, s));
+  k_fill<int32_t><<<grid_small((long long)g->qcap), kNT, 0, s>>>(g->queue.p, (long long)g->qcap, -1);
+  DFPR_LAUNCHED();
+}
+
+template <class P>
+dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st,
+                         cudaEvent_t e0, cudaEvent_t e1, bool mark_only) {
+  cudaStream_t s = g->stream;
+  Args<P> a = make_args<P>(g, p);
+  set_vectors<P>(g, a);
+  a.mark_only = mark_only ? 1 : 0;
+  long long* nsi = nullptr;
+  long long seeded = 0;
+  if (kind == kRunDF) {
+    nsi = prepare_marking<P>(g, a);
+  } else {
+    seeded = g->n;
+  }
+  const long long work_cap = (long long)p.max_iter * (long long)g->n;
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, work_cap, seeded, 1);
+  DFPR_LAUNCHED();
+  if (seeded) {
+    k_seed_all<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p, g->queue.p);
+    DFPR_LAUNCHED();
+  }
+  if (a.teleport) {
+    // the dead-end mass enters every vertex: computed once per call here
+    DFPR_CUDA(cudaMemsetAsync(&g->ctl.p->dsum, 0, sizeof(double), s));
+    k_dangling<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, a.R, &g->ctl.p->dsum);
+    DFPR_LAUNCHED();
+  }
+  const int grid = persistent_grid(g, p, (const void*)k_worklist<P>);
+  DFPR_CUDA(cudaEventRecord(e0, s));  // the stats time the persistent kernel alone
+  k_worklist<P><<<grid, kNT, 0, s>>>(a);
+  DFPR_LAUNCHED();
+  DFPR_CUDA(cudaEventRecord(e1, s));
+  CtlHost h = read_ctl(g);
+  if (st) fill_stats(h.c, st);
+  const bool clean = h.c.status == 0 && h.c.pending <= 0 && !mark_only;
+  if (!clean && !mark_only) reset_worklist_state(g);
+  return h.c.status ? (dfpr_status)h.c.status : DFPR_OK;
+}
+
+template <class P>
+dfpr_status run_round(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st,
+                      cudaEvent_t e0, cudaEvent_t e1) {
+  cudaStream_t s = g->stream;
+  Args<P> a = make_args<P>(g, p);
+  set_vectors<P>(g, a);
+  long long* nsi = nullptr;
+  if (kind == kRunDF) nsi = prepare_marking<P>(g, a);
+  DFPR_CUDA(cudaEventRecord(e0, s));
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 1);
+  DFPR_LAUNCHED();
+  g->pass_ctr.ensure((size_t)p.max_iter + 1, s);
+  a.pass_ctr = g->pass_ctr.p;
+  DFPR_CUDA(cudaMemsetAsync(g->pass_ctr.p, 0, sizeof(unsigned long long) * (p.max_iter + 1), s));
+  // marking-item completion flags (the helping rule)
+  if (kind == kRunDF) {
+    const long long nsrc_items = (long long)read_word(g, nsi, sizeof(long long));
+    const long long items = nsrc_items + (g->pend.n_dst + 31) / 32;
+    g->item_done.ensure((size_t)items + 1, s);
+    a.item_done = g->item_done.p;
+    DFPR_CUDA(cudaMemsetAsync(g->item_done.p, 0, sizeof(uint32_t) * (items + 1), s));
+  } else {
+    // ND / static: every vertex is affected and not converged from the start
+    DFPR_CUDA(cudaMemsetAsync(g->va_bits.p, 0xff, sizeof(uint32_t) * g->va_bits.count, s));
+    DFPR_CUDA(cudaMemsetAsync(g->rc_bits.p, 0xff, sizeof(uint32_t) * g->rc_bits.count, s));
+    k_seed_round<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->affected_list.p, g->ctl.p);
+    DFPR_LAUNCHED();
+  }
+  const int grid = persistent_grid(g, p, (const void*)k_round<P>);
+  k_round<P><<<grid, kNT, 0, s>>>(a);
+  DFPR_LAUNCHED();
+  DFPR_CUDA(cudaEventRecord(e1, s));
+  CtlHost h = read_ctl(g);
+  if (st) {
+    fill_stats(h.c, st);
+    st->passes = (int32_t)h.c.pad[0];
+    st->affected = h.c.len;
+  }
+  dfpr_status status = h.c.status ? (dfpr_status)h.c.status : DFPR_OK;
+  if (status == DFPR_OK && h.c.nc > 0) status = DFPR_ENOTCONV;
+  // clear flags and list for the next call
+  k_clear_list<<<grid_small(h.c.len), kNT, 0, s>>>(g->affected_list.p, h.c.len, g->va_bits.p, g->rc_bits.p);
+  DFPR_LAUNCHED();
+  if (kind != kRunDF) {
+    DFPR_CUDA(cudaMemsetAsync(g->va_bits.p, 0, sizeof(uint32_t) * g->va_bits.count, s));
+    DFPR_CUDA(cudaMemsetAsync(g->rc_bits.p, 0, sizeof(uint32_t) * g->rc_bits.count, s));
+  }
+  return status;
+}
+
+template <class T>
+void swap_arrays(DevArray<T>& x, DevArray<T>& y) {
+  std::swap(x.p, y.p);
+  std::swap(x.count, y.count);
+  std::swap(x.s, y.s);
+  std::swap(x.rec, y.rec);
+}
+
+template <class P>
+void swap_vectors(dfpr_graph* g);
+template <>
+void swap_vectors<P64>(dfpr_graph* g) {
+  swap_arrays(g->R64, g->R64b);
+  swap_arrays(g->C64, g->C64b);
+}
+template <>
+void swap_vectors<P32>(dfpr_graph* g) {
+  swap_arrays(g->R32, g->R32b);
+  swap_arrays(g->C32, g->C32b);
+}
+
+template <class P>
+void second_vectors(dfpr_graph* g, typename P::val** R2, typename P::val** C2);
+template <>
+void second_vectors<P64>(dfpr_graph* g, double** R2, double** C2) {
+  if (!g->R64b.p) {
+    g->R64b.reset(g->n, g->stream);
+    g->C64b.reset(g->n, g->stream);
+  }
+  *R2 = g->R64b.p;
+  *C2 = g->C64b.p;
+}
+template <>
+void second_vectors<P32>(dfpr_graph* g, float** R2, float** C2) {
+  if (!g->R32b.p) {
+    g->R32b.reset(g->n, g->stream);
+    g->C32b.reset(g->n, g->stream);
+  }
+  *R2 = g->R32b.p;
+  *C2 = g->C32b.p;
+}
+
+// Jacobi schedule: host loop of one kernel per iteration, L-inf stop test.
+template <class P>
+dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st,
+                       cudaEvent_t e0, cudaEvent_t e1) {
+  cudaStream_t s = g->stream;
+  using V = typename P::val;
+  V *R2 = nullptr, *C2 = nullptr;
+  second_vectors<P>(g, &R2, &C2);
+  Args<P> a = make_args<P>(g, p);
+  set_vectors<P>(g, a);
+  long long* nsi = nullptr;
+  if (kind == kRunDF) nsi = prepare_marking<P>(g, a);
+  DFPR_CUDA(cudaEventRecord(e0, s));
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 0);
+  DFPR_LAUNCHED();
+  const bool df = kind == kRunDF;
+  long long count = g->n;
+  if (df) {
+    // unaffected vertices keep R_prev in both vectors
+    DFPR_CUDA(cudaMemcpyAsync(R2, a.R, sizeof(V) * g->n, cudaMemcpyDeviceToDevice, s));
+    DFPR_CUDA(cudaMemcpyAsync(C2, a.C, sizeof(V) * g->n, cudaMemcpyDeviceToDevice, s));
+    k_mark_list<P><<<grid_small(32ll * g->n), kNT, 0, s>>>(a);
+    DFPR_LAUNCHED();
+    count = (long long)read_word(g, &g->ctl.p->len, sizeof(long long));
+  }
+  const int grid = persistent_grid(g, p, (const void*)k_jacobi<P>);
+  int it = 0;
+  double last = 0.0;
+  bool converged = false;
+  for (; it < p.max_iter; ++it) {
+    DFPR_CUDA(cudaMemsetAsync(&g->ctl.p->max_change_bits, 0, sizeof(unsigned long long), s));
+    if (a.teleport) {
+      DFPR_CUDA(cudaMemsetAsync(&g->ctl.p->dsum, 0, sizeof(double), s));
+      k_dangling<V><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, a.R, &g->ctl.p->dsum);
+      DFPR_LAUNCHED();
+    }
+    k_jacobi<P><<<grid, kNT, 0, s>>>(a, a.R, a.C, R2, C2, df ? g->affected_list.p : nullptr, count,
+                                     df ? 1 : 0);
+    DFPR_LAUNCHED();
+    DFPR_CUDA(cudaMemcpyAsync(g->pinned, &g->ctl.p->max_change_bits, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, s));
+    DFPR_CUDA(cudaMemcpyAsync(g->pinned + 1, &g->ctl.p->len, sizeof(long long),
+                              cudaMemcpyDeviceToHost, s));
+    DFPR_CUDA(cudaStreamSynchronize(s));
+    memcpy(&last, &g->pinned[0], sizeof last);
+    if (df) count = (long long)g->pinned[1];
+    // swap R <-> R2, C <-> C2
+    swap_vectors<P>(g);
+    std::swap(R2, a.R);
+    std::swap(C2, a.C);
+    if (last <= p.tol) {
+      converged = true;
+      ++it;
+      break;
+    }
+  }
+  DFPR_CUDA(cudaEventRecord(e1, s));
+  CtlHost h = read_ctl(g);
+  if (st) {
+    fill_stats(h.c, st);
+    st->passes = it;
+    st->residual_linf = last;
+    st->affected = df ? count : g->n;
+  }
+  if (df) {
+    k_clear_list<<<grid_small(count), kNT, 0, s>>>(g->affected_list.p, count, g->va_bits.p, nullptr);
+    DFPR_LAUNCHED();
+  }
+  return converged ? DFPR_OK : DFPR_ENOTCONV;
+}
+
+template <class P>
+void normalize_ranks(dfpr_graph* g) {
+  cudaStream_t s = g->stream;
+  double* sum = &g->ctl.p->dsum;
+  DFPR_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), s));
+  typename P::val *R, *C;
+  if constexpr (sizeof(typename P::val) == 8) {
+    R = (typename P::val*)g->R64.p;
+    C = (typename P::val*)g->C64.p;
+  } else {
+    R = (typename P::val*)g->R32.p;
+    C = (typename P::val*)g->C32.p;
+  }
+  k_sum_ranks<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, R, sum);
+  DFPR_LAUNCHED();
+  k_scale<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, R, C, sum);
+  DFPR_LAUNCHED();
+}
+
+template <class P>
+dfpr_status run_any(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st) {
+  cudaStream_t s = g->stream;
+  cudaEvent_t e0, e1;
+  DFPR_CUDA(cudaEventCreate(&e0));
+  DFPR_CUDA(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } guard{e0, e1};
+  if (kind == kRunStatic) reset_ranks(g);
+  g->epoch += 1;
+  if (g->epoch == 0) {  // wrapped: clear epochs so that no vertex looks current
+    DFPR_CUDA(cudaMemsetAsync(g->ep.p, 0, sizeof(uint32_t) * g->n, s));
+    g->epoch = 1;
+  }
+  dfpr_status r;
+  if (p.mode == DFPR_MODE_WORKLIST) r = run_worklist<P>(g, p, kind, st, e0, e1, false);
+  else if (p.mode == DFPR_MODE_ROUND) r = run_round<P>(g, p, kind, st, e0, e1);
+  else r = run_jacobi<P>(g, p, kind, st, e0, e1);
+  if (p.normalize && r == DFPR_OK) normalize_ranks<P>(g);
+  float ms = 0.f;
+  DFPR_CUDA(cudaEventSynchronize(e1));
+  DFPR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  if (st) {
+    st->ms = ms;
+    st->status = r;
+  }
+  // the pending change set has been consumed
+  g->pend.n_src = 0;
+  g->pend.n_dst = 0;
+  return r;
+}
+
+}  // namespace
+
+void alloc_iteration_state(dfpr_graph* g) {
+  cudaStream_t s = g->stream;
+  const int32_t n = g->n;
+  if (g->cfg.precision == DFPR_FP64) {
+    g->R64.reset(n, s);
+    g->C64.reset(n, s);
+    g->X64.reset(n, s);
+  } else {
+    g->R32.reset(n, s);
+    g->C32.reset(n, s);
+    g->X32.reset(n, s);
+  }
+  g->ep.reset(n, s);
+  DFPR_CUDA(cudaMemsetAsync(g->ep.p, 0, sizeof(uint32_t) * n, s));
+  g->epoch = 0;
+  g->state.reset(((size_t)n + 15) / 16, s);
+  DFPR_CUDA(cudaMemsetAsync(g->state.p, 0, sizeof(uint32_t) * g->state.count, s));
+  unsigned long long q = 1024;
+  while (q < 2ull * (unsigned long long)n) q <<= 1;
+  g->qcap = q;
+  g->queue.reset(q, s);
+  k_fill<int32_t><<<grid_small((long long)q), kNT, 0, s>>>(g->queue.p, (long long)q, -1);
+  DFPR_LAUNCHED();
+  g->ctl.reset(1, s);
+  DFPR_CUDA(cudaMemsetAsync(g->ctl.p, 0, sizeof(DfCtl), s));
+  g->affected_list.reset(n, s);
+  k_fill<int32_t><<<grid_small(n), kNT, 0, s>>>(g->affected_list.p, n, -1);
+  DFPR_LAUNCHED();
+  g->va_bits.reset(((size_t)n + 31) / 32, s);
+  g->rc_bits.reset(((size_t)n + 31) / 32, s);
+  DFPR_CUDA(cudaMemsetAsync(g->va_bits.p, 0, sizeof(uint32_t) * g->va_bits.count, s));
+  DFPR_CUDA(cudaMemsetAsync(g->rc_bits.p, 0, sizeof(uint32_t) * g->rc_bits.count, s));
+}
+
+void reset_ranks(dfpr_graph* g) {
+  cudaStream_t s = g->stream;
+  if (g->cfg.precision == DFPR_FP64)
+    k_init_ranks<double><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, g->C64.p);
+  else
+    k_init_ranks<float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, g->C32.p);
+  DFPR_LAUNCHED();
+}
+
+double rank_sum(dfpr_graph* g) {
+  cudaStream_t s = g->stream;
+  double* sum = (double*)(g->host_sync.p + 8);
+  DFPR_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), s));
+  if (g->cfg.precision == DFPR_FP64)
+    k_sum_ranks<double><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->R64.p, sum);
+  else
+    k_sum_ranks<float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->R32.p, sum);
+  DFPR_LAUNCHED();
+  unsigned long long bits = read_word(g, sum, sizeof(double));
+  double d;
+  memcpy(&d, &bits, sizeof d);
+  return d;
+}
+
+dfpr_status run_iteration(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st) {
+  if (g->cfg.precision == DFPR_FP64) return run_any<P64>(g, p, kind, st);
+  return run_any<P32>(g, p, kind, st);
+}
+
+void initial_affected(dfpr_graph* g, uint8_t* affected_dev, long long* count) {
+  cudaStream_t s = g->stream;
+  dfpr_params p;
+  dfpr_default_params(&p);
+  cudaEvent_t e0, e1;
+  DFPR_CUDA(cudaEventCreate(&e0));
+  DFPR_CUDA(cudaEventCreate(&e1));
+  dfpr_status r;
+  if (g->cfg.precision == DFPR_FP64) r = run_worklist<P64>(g, p, kRunDF, nullptr, e0, e1, true);
+  else r = run_worklist<P32>(g, p, kRunDF, nullptr, e0, e1, true);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DFPR_REQUIRE(r == DFPR_OK, r, "dfpr_initial_affected: marking did not complete");
+  k_export_state<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p, affected_dev);
+  DFPR_LAUNCHED();
+  CtlHost h = read_ctl(g);
+  if (count) *count = (long long)h.c.tail;
+  // the marking pushed every affected vertex once: undo it
+  reset_worklist_state(g);
+}
+
+}  // namespace dfpr

@@ -1,0 +1,26 @@
+// Rank iterations: Dynamic Frontier, naive-dynamic and static schedules.
+#pragma once
+#include "common.cuh"
+
+namespace dfpr {
+
+enum RunKind { kRunDF = 0, kRunND = 1, kRunStatic = 2 };
+
+// Runs one rank computation on g (see dfpr_df_pagerank / dfpr_nd_pagerank /
+// dfpr_static_pagerank). Returns the status of the iteration (OK, ENOTCONV,
+// ETIMEOUT); throws Fail on CUDA or argument errors.
+dfpr_status run_iteration(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st);
+
+// Initial marking only: affected flags (device, n bytes) and their count.
+void initial_affected(dfpr_graph* g, uint8_t* affected_dev, long long* count);
+
+// Allocates the iteration state of g (ranks, flags, queue, control block).
+void alloc_iteration_state(dfpr_graph* g);
+
+// Sets every rank to 1/n and the contributions to R / outdeg.
+void reset_ranks(dfpr_graph* g);
+
+// FP64 sum of the ranks.
+double rank_sum(dfpr_graph* g);
+
+}  // namespace dfpr
