@@ -335,16 +335,26 @@ __global__ void k_contrib_all(int32_t n, const RowDesc* __restrict__ rows, const
   }
 }
 
+// Appends the groups' sources and the deletion targets to the pending change
+// set; cap_src / cap_dst are the room the host reserved (writes beyond are
+// dropped and flagged, never performed).
 __global__ void k_append_pending(const uint32_t* __restrict__ gid_total, long long nrc,
                                  const int32_t* __restrict__ gowner,
                                  const unsigned long long* __restrict__ rc, int bits,
                                  const uint32_t* __restrict__ delf, const uint32_t* __restrict__ delpre,
-                                 int32_t* psrc, int32_t* pdst) {
+                                 int32_t* psrc, long long cap_src, int32_t* pdst, long long cap_dst,
+                                 unsigned long long* err) {
   const long long ng = *gid_total;
   const unsigned long long mask = (1ull << bits) - 1;
   GRID_STRIDE(i, nrc) {
-    if (i < ng) psrc[i] = gowner[i];
-    if (delf[i]) pdst[delpre[i]] = (int32_t)((rc[i] >> 1) & mask);
+    if (i < ng) {
+      if (i < cap_src) psrc[i] = gowner[i];
+      else atomicOr(err, 2ull);
+    }
+    if (delf[i]) {
+      if ((long long)delpre[i] < cap_dst) pdst[delpre[i]] = (int32_t)((rc[i] >> 1) & mask);
+      else atomicOr(err, 2ull);
+    }
   }
 }
 
@@ -547,13 +557,14 @@ void apply_direction(dfpr_graph* g, Rows& dir, const unsigned long long* rc, lon
   DFPR_LAUNCHED();
   scan_exclusive_i64(newdeg, soff, nrc, soff + nrc, sc, s);
   scan_exclusive_i64(work, woff, nrc, woff + nrc, sc, s);
-  // read back: overflow flag, group count, merged size S, work W
+  // read back: overflow flag, group count, merged size S, work W (the group
+  // count is a 4-byte word: clear the 8-byte host slot before the copy lands)
+  g->pinned[1] = 0;
   DFPR_CUDA(cudaMemcpyAsync(g->pinned, words + kWOverflow, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, s));
   DFPR_CUDA(cudaMemcpyAsync(g->pinned + 1, gid + nrc, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   DFPR_CUDA(cudaMemcpyAsync(g->pinned + 2, soff + nrc, sizeof(long long), cudaMemcpyDeviceToHost, s));
   DFPR_CUDA(cudaMemcpyAsync(g->pinned + 3, woff + nrc, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  g->pinned[1] = 0;
   DFPR_CUDA(cudaStreamSynchronize(s));
   const bool overflow = g->pinned[0] != 0;
   const long long ngroups = (long long)(uint32_t)g->pinned[1];
@@ -587,9 +598,15 @@ void apply_direction(dfpr_graph* g, Rows& dir, const unsigned long long* rc, lon
   const long long nd = g->last_real_del;
   grow_keep(g->pend.src, g->pend.n_src, g->pend.n_src + ngroups, s);
   grow_keep(g->pend.dst, g->pend.n_dst, g->pend.n_dst + nd, s);
+  DFPR_CUDA(cudaMemsetAsync(words + kWErr, 0, sizeof(unsigned long long), s));
   k_append_pending<<<gr, NT, 0, s>>>(gid + nrc, nrc, gowner, rc, bits, delf, delpre,
-                                     g->pend.src.p + g->pend.n_src, g->pend.dst.p + g->pend.n_dst);
+                                     g->pend.src.p + g->pend.n_src,
+                                     (long long)g->pend.src.count - g->pend.n_src,
+                                     g->pend.dst.p + g->pend.n_dst,
+                                     (long long)g->pend.dst.count - g->pend.n_dst, words + kWErr);
   DFPR_LAUNCHED();
+  DFPR_REQUIRE(read_word(g, words + kWErr, 8) == 0, DFPR_ECUDA,
+               "apply_batch: pending change set larger than reserved (internal error)");
   g->pend.n_src += ngroups;
   g->pend.n_dst += nd;
 }
