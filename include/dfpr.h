@@ -223,6 +223,36 @@ dfpr_status dfpr_set_allocator(dfpr_alloc_fn alloc, dfpr_free_fn free_fn, void* 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* dfpr_last_error(void);
 
+/*
+ * Static PageRank (every rank starts at 1/n, Jacobi iteration of Eq. 1 until
+ * the largest change is <= tol or max_iter iterations) over a graph the caller
+ * already holds on the device, without allocating any device memory. The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc / cudaFree, for example code working inside a memory budget
+ * that another component (a framework's pool allocator, a server's fixed
+ * arena) owns entirely, or code that must not trigger the device-wide
+ * synchronisation those calls imply.
+ *
+ * Arguments (all arrays are device pointers on the current device):
+ *   n           vertices, 1 <= n <= 1,048,576 (larger n returns EINVAL)
+ *   in_offsets  int64[n + 1], in-edge row offsets (CSC); in_idx int32[m] the
+ *               sources of each vertex's in-edges; out_degree int32[n]
+ *   ranks       double[n], output
+ *   iterations  host int32 (may be NULL): iterations performed
+ *   cuda_stream the cudaStream_t to run on (NULL: the legacy default stream)
+ * Scratch (a second rank vector, two contribution vectors and a reduction
+ * word) lives in one fixed __device__ array of 24 MiB + 256 bytes that every
+ * GPU loading this library keeps until the process exits. The first call on a
+ * device looks up that array's device address (with the device current), so
+ * make the first call before any stream capture. All calls share the array:
+ * calls that overlap on the GPU race and give wrong results. Returns OK,
+ * ENOTCONV (cap reached; ranks are the last iterate), EINVAL, ECUDA.
+ */
+dfpr_status dfpr_static_pagerank_noalloc(int32_t n, const int64_t* in_offsets,
+                                         const int32_t* in_idx, const int32_t* out_degree,
+                                         double alpha, double tol, int32_t max_iter,
+                                         double* ranks, int32_t* iterations, void* cuda_stream);
+
 /* Number of CUDA kernels the library has launched in this process so far
  * (a diagnostic counter; no paper counterpart). */
 int64_t dfpr_kernel_launches(void);

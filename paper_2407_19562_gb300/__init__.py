@@ -111,6 +111,9 @@ def load():
             "dfpr_last_error": (ctypes.c_char_p, []),
             "dfpr_version": (i32, []),
             "dfpr_kernel_launches": (i64, []),
+            "dfpr_static_pagerank_noalloc": (st, [i32, vp, vp, vp, ctypes.c_double,
+                                                  ctypes.c_double, i32, vp,
+                                                  ctypes.POINTER(i32), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
