@@ -120,25 +120,37 @@ struct Rows {
   DevArray<unsigned long long> tail;  // 1: next free position of the spare area
 };
 
+// A counter alone on its own 256-byte line: the queue counters are hit by
+// every warp, and counters sharing a line would serialise at one L2 slice.
+struct __align__(256) HotU64 {
+  unsigned long long v;
+  unsigned long long pad_[31];
+};
+struct __align__(256) HotI64 {
+  long long v;
+  long long pad_[31];
+};
+
 // Device control block of one rank iteration (all counters 64-bit).
 struct DfCtl {
-  unsigned long long head;        // queue positions claimed by consumers
-  unsigned long long tail;        // queue positions claimed by producers
-  long long avail;                // pushed but not yet claimed
-  long long pending;              // queued + running vertices + open marking items
-  unsigned long long mark_next;   // next marking item to claim
-  unsigned long long n_src_items; // marking items over out-rows of sources
-  unsigned long long n_items;     // all marking items
-  unsigned int status;            // 0, or the dfpr_status that stopped the workers
-  unsigned int abort;             // 1: workers stop
-  unsigned long long processed, edges, expansions, edges_marked, pushes, affected;
+  HotU64 head;        // queue positions claimed by consumers
+  HotU64 tail;        // queue positions claimed by producers
+  HotI64 avail;       // pushed but not yet claimed
+  HotI64 pending;     // queued + running vertices + open marking items
+  HotU64 mark_next;   // next marking item to claim
+  HotU64 processed;   // recomputations (work cap)
+  HotI64 len;         // affected-list length (round / jacobi)
+  HotI64 nc;          // vertices flagged not converged (round)
+  unsigned long long n_src_items;  // marking items over out-rows of sources
+  unsigned long long n_items;      // all marking items
+  unsigned int status;             // 0, or the dfpr_status that stopped the workers
+  unsigned int abort;              // 1: workers stop
+  unsigned long long edges, expansions, edges_marked, pushes, affected;
   unsigned long long max_change_bits;  // max |change| of a recomputation (bits of a double)
-  long long work_cap;             // cap on recomputations (worklist)
-  unsigned long long t_start;     // globaltimer at launch
-  long long len;                  // affected-list length (round / jacobi)
-  long long nc;                   // vertices flagged not converged (round)
-  double dsum;                    // rank held by dead ends (teleport)
-  unsigned long long pad[4];
+  long long work_cap;              // cap on recomputations (worklist)
+  unsigned long long t_start;      // globaltimer at launch
+  double dsum;                     // rank held by dead ends (teleport)
+  unsigned long long passes;       // round: passes reached
 };
 
 struct Pending {

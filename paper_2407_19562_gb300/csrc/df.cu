@@ -173,15 +173,41 @@ __device__ void stop_with(const Args<P>& a, unsigned status) {
   atomicExch(&a.ctl->abort, 1u);
 }
 
+// Row descriptor through the read-only path (rows do not change during a kernel).
+__device__ __forceinline__ RowDesc load_row(const RowDesc* p) {
+  const longlong2 x = __ldg(reinterpret_cast<const longlong2*>(p));
+  RowDesc r;
+  r.off = x.x;
+  r.deg = (int)(x.y & 0xffffffffll);
+  r.cap = (int)(x.y >> 32);
+  return r;
+}
+
+// Last index j in [0, 32) with s_excl[j] <= e (s_excl nondecreasing, s_excl[0] = 0).
+__device__ __forceinline__ int owner_of(const int* s_excl, int e) {
+  int lo = 0, hi = 32;
+#pragma unroll
+  for (int step = 0; step < 5; ++step) {
+    const int mid = (lo + hi) >> 1;
+    if (s_excl[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kUnroll = 4;  // 32-edge chunks with loads in flight at once
+
 // Warp-cooperative edge-balanced gather: lane i owns vertex v_i (or -1).
-// Returns sum_{u in in(v_i)} C[u] in lane i.
+// Returns sum_{u in in(v_i)} C[u] in lane i. The in-edges of the 32 vertices
+// are walked as one list, kUnroll chunks of 32 at a time: first every chunk's
+// ids are loaded, then every chunk's contributions, then each chunk is reduced
+// by a segmented warp scan whose segment tails add into s_acc[owner].
 template <class P>
 __device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl, long long* s_off,
                                   typename P::acc* s_acc, WarpStats& st) {
   int deg = 0;
   long long off = 0;
   if (v >= 0) {
-    const RowDesc r = a.in_rows[v];
+    const RowDesc r = load_row(a.in_rows + v);
     deg = r.deg;
     off = r.off;
   }
@@ -192,60 +218,95 @@ __device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl
     if (lane >= d) incl += y;
   }
   const int total = __shfl_sync(kFull, incl, 31);
+  __syncwarp();
   s_excl[lane] = incl - deg;
   s_off[lane] = off;
   s_acc[lane] = P::zero();
   __syncwarp();
-  for (int base = 0; base < total; base += 32) {
-    const int e = base + lane;
-    const bool valid = e < total;
-    int owner = 0;
-    typename P::acc x = P::zero();
-    if (valid) {
-      int lo = 0, hi = 32;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_excl[mid] <= e) lo = mid; else hi = mid;
-      }
-      owner = lo;
-      const int u = a.in_edges[s_off[owner] + (e - s_excl[owner])];
-      x = P::from(P::load(a.C + u));
-    }
-    const int key = valid ? owner : 32 + lane;
+  for (int base = 0; base < total; base += 32 * kUnroll) {
+    int owner[kUnroll];
+    int uid[kUnroll];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const typename P::acc y = P::shfl_up(x, d);
-      const int k2 = __shfl_up_sync(kFull, key, d);
-      if (lane >= d && k2 == key) x = P::add(x, y);
+    for (int k = 0; k < kUnroll; ++k) {
+      const int e = base + k * 32 + lane;
+      owner[k] = -1;
+      uid[k] = 0;
+      if (e < total) {
+        const int o = owner_of(s_excl, e);
+        owner[k] = o;
+        uid[k] = __ldg(a.in_edges + s_off[o] + (e - s_excl[o]));
+      }
     }
-    const int knext = __shfl_down_sync(kFull, key, 1);
-    if (valid && (lane == 31 || knext != key)) s_acc[owner] = P::add(s_acc[owner], x);
-    __syncwarp();
+    typename P::val xv[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k)
+      xv[k] = owner[k] >= 0 ? P::load(a.C + uid[k]) : (typename P::val)0;
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      if (base + k * 32 >= total) break;  // warp-uniform
+      typename P::acc x = P::from(xv[k]);
+      const int key = owner[k] >= 0 ? owner[k] : 32 + lane;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const typename P::acc y = P::shfl_up(x, d);
+        const int k2 = __shfl_up_sync(kFull, key, d);
+        if (lane >= d && k2 == key) x = P::add(x, y);
+      }
+      const int knext = __shfl_down_sync(kFull, key, 1);
+      if (owner[k] >= 0 && (lane == 31 || knext != key)) s_acc[key] = P::add(s_acc[key], x);
+      __syncwarp();
+    }
   }
   st.edges += (unsigned long long)deg;
   return s_acc[lane];
 }
 
-// Pushes t for every lane with need (warp-uniform call). Lane 0 performs all
-// counter updates of the warp, so that pending increments precede this warp's
-// later decrements in program order.
+// Per-warp buffer of queue insertions in shared memory, flushed to the ring
+// once per batch (or when full), so that a batch pays one fence and one
+// round of counter atomics for all its insertions.
+constexpr int kPushCap = 256;
+struct PushBuf {
+  int* items;
+  int* cnt;   // items buffered
+  int* nnew;  // of which newly queued (they add to `pending`)
+  int* owed;  // completions not yet subtracted from `pending`
+};
+
+// Applies this warp's deferred completions to `pending` (lane 0). Deferring a
+// decrement only over-counts, so it is always safe; an idle warp settles its
+// debt before it tests for termination.
 template <class P>
-__device__ bool push_warp(const Args<P>& a, int t, bool need, bool count_pending, int lane,
-                          WarpStats& st) {
-  const unsigned b = __ballot_sync(kFull, need);
-  if (!b) return true;
-  const int cnt = __popc(b);
+__device__ void settle_owed(const Args<P>& a, PushBuf pb, int lane) {
+  __syncwarp();
+  if (lane == 0 && *pb.owed) {
+    atomic_add_ll(&a.ctl->pending.v, -(long long)*pb.owed);
+    *pb.owed = 0;
+  }
+  __syncwarp();
+}
+
+template <class P>
+__device__ bool buf_flush(const Args<P>& a, PushBuf pb, int lane, WarpStats& st) {
+  __syncwarp();
+  const int cnt = *pb.cnt;
+  if (cnt == 0) return true;
+  const int nnew = *pb.nnew;
   unsigned long long base = 0;
   if (lane == 0) {
-    if (count_pending) atomic_add_ll(&a.ctl->pending, cnt);
-    base = atomicAdd(&a.ctl->tail, (unsigned long long)cnt);
-    st.pushes += cnt;
+    // `pending` grows before any of these items becomes visible in the ring,
+    // so it cannot reach zero while they are outstanding; the warp's deferred
+    // completions ride on the same atomic
+    const long long delta = (long long)nnew - (long long)*pb.owed;
+    *pb.owed = 0;
+    if (delta) atomic_add_ll(&a.ctl->pending.v, delta);
+    __threadfence();
+    base = atomicAdd(&a.ctl->tail.v, (unsigned long long)cnt);
+    st.pushes += (unsigned long long)cnt;
   }
   base = __shfl_sync(kFull, base, 0);
   bool ok = true;
-  if (need) {
-    const unsigned long long pos = base + __popc(b & lanemask_lt());
-    int* slot = a.queue + (pos & a.qmask);
+  for (int i = lane; i < cnt; i += 32) {
+    int* slot = a.queue + ((base + (unsigned long long)i) & a.qmask);
     unsigned spins = 0;
     while (ld_volatile(slot) != -1) {  // slot still held by a slow consumer
       if ((++spins & 255u) == 0 && timed_out(a)) {
@@ -255,24 +316,89 @@ __device__ bool push_warp(const Args<P>& a, int t, bool need, bool count_pending
       }
       __nanosleep(64);
     }
-    if (ok) *(volatile int*)slot = t;
+    if (!ok) break;
+    *(volatile int*)slot = pb.items[i];
   }
-  __threadfence();
   __syncwarp();
-  if (lane == 0) atomic_add_ll(&a.ctl->avail, cnt);
+  if (lane == 0) {
+    atomic_add_ll(&a.ctl->avail.v, cnt);  // consumers wait on the slots themselves
+    *pb.cnt = 0;
+    *pb.nnew = 0;
+  }
+  __syncwarp();
   return __all_sync(kFull, ok);
 }
 
-// Sets the queued bit of t (lanes with valid) and pushes vertices that were idle.
+// Buffers t for every lane with need (warp-uniform call).
 template <class P>
-__device__ void mark_push(const Args<P>& a, int t, bool valid, int lane, WarpStats& st) {
-  bool need = false;
-  if (valid) {
-    const unsigned sh = (unsigned)(t & 15) * 2u;
-    const unsigned old = atomicOr(a.state + (t >> 4), 1u << sh);
-    need = ((old >> sh) & 3u) == 0u;
+__device__ void buf_push(const Args<P>& a, PushBuf pb, int t, bool need, bool is_new, int lane,
+                         WarpStats& st) {
+  const unsigned b = __ballot_sync(kFull, need);
+  if (!b) return;
+  const int k = __popc(b);
+  if (*pb.cnt + k > kPushCap) buf_flush(a, pb, lane, st);
+  const int c = *pb.cnt;
+  if (need) pb.items[c + __popc(b & lanemask_lt())] = t;
+  __syncwarp();
+  if (lane == 0) {
+    *pb.cnt = c + k;
+    if (is_new) *pb.nnew += k;
   }
-  push_warp(a, t, need, true, lane, st);
+  __syncwarp();
+}
+
+// Marks t (lanes with valid): sets its queued bit and buffers it when it was
+// idle. A plain load first skips the atomic when the bit is already set; that
+// is safe because the caller fenced its rank writes before marking, and a
+// worker clears the bit (and fences) before reading contributions.
+template <class P>
+__device__ __forceinline__ bool mark_one(const Args<P>& a, int t, bool valid, unsigned word) {
+  if (!valid) return false;
+  const unsigned sh = (unsigned)(t & 15) * 2u;
+  if ((word >> sh) & 1u) return false;
+  const unsigned old = atomicOr(a.state + (t >> 4), 1u << sh);
+  return ((old >> sh) & 3u) == 0u;
+}
+
+// Marks the out-neighbours of every lane's vertex whose `od` > 0 (edge-balanced
+// like the gather, kUnroll chunks in flight).
+template <class P>
+__device__ void expand_rows(const Args<P>& a, int od, long long oo, int lane, int* s_excl,
+                            long long* s_off, PushBuf pb, WarpStats& st) {
+  int incl = od;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  if (total == 0) return;
+  __syncwarp();
+  s_excl[lane] = incl - od;
+  s_off[lane] = oo;
+  __syncwarp();
+  for (int base = 0; base < total; base += 32 * kUnroll) {
+    int t[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int e = base + k * 32 + lane;
+      t[k] = -1;
+      if (e < total) {
+        const int o = owner_of(s_excl, e);
+        t[k] = __ldg(a.out_edges + s_off[o] + (e - s_excl[o]));
+      }
+    }
+    unsigned wv[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) wv[k] = t[k] >= 0 ? ld_volatile(a.state + (t[k] >> 4)) : 0u;
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      if (base + k * 32 >= total) break;  // warp-uniform
+      const bool need = mark_one(a, t[k], t[k] >= 0, wv[k]);
+      buf_push(a, pb, t[k], need, true, lane, st);
+    }
+  }
+  if (lane == 0) st.edges_marked += (unsigned long long)total;
 }
 
 // Marking item: a chunk of a source's out-row, or up to 32 deletion targets.
@@ -289,13 +415,13 @@ __device__ void do_mark_item(const Args<P>& a, long long item, int lane, WarpSta
     }
     const int u = a.mark_src[lo];
     const long long chunk = item - a.mark_choff[lo];
-    const RowDesc r = a.out_rows[u];
+    const RowDesc r = load_row(a.out_rows + u);
     const long long beg = chunk * kMarkChunk;
     const long long end = min((long long)r.deg, beg + kMarkChunk);
     for (long long e0 = beg; e0 < end; e0 += 32) {
       const long long e = e0 + lane;
       const bool valid = e < end;
-      const int t = valid ? a.out_edges[r.off + e] : 0;
+      const int t = valid ? __ldg(a.out_edges + r.off + e) : 0;
       mark(t, valid);
     }
     if (lane == 0) st.edges_marked += (unsigned long long)max(0ll, end - beg);
@@ -343,29 +469,41 @@ __device__ __forceinline__ typename P::val finish_rank(const Args<P>& a, typenam
 // ---------------------------------------------------------------------------
 
 template <class P>
-__global__ void __launch_bounds__(kNT) k_worklist(Args<P> a) {
+__global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   __shared__ int s_excl[kWPB][32];
   __shared__ long long s_off[kWPB][32];
   __shared__ typename P::acc s_acc[kWPB][32];
+  __shared__ int s_push[kWPB][kPushCap];
+  __shared__ int s_pcnt[kWPB][3];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   DfCtl* ctl = a.ctl;
   WarpStats st = {0, 0, 0, 0, 0, 0.0};
-  auto mark = [&](int t, bool valid) { mark_push(a, t, valid, lane, st); };
+  if (lane == 0) {
+    s_pcnt[w][0] = 0;
+    s_pcnt[w][1] = 0;
+    s_pcnt[w][2] = 0;
+  }
+  __syncwarp();
+  const PushBuf pb{s_push[w], &s_pcnt[w][0], &s_pcnt[w][1], &s_pcnt[w][2]};
+  unsigned long long local_processed = 0;  // lane 0: recomputations not yet added to the cap count
+  auto mark = [&](int t, bool valid) {
+    const unsigned word = valid ? ld_volatile(a.state + (t >> 4)) : 0u;
+    const bool need = mark_one(a, t, valid, word);
+    buf_push(a, pb, t, need, true, lane, st);
+  };
 
   // Stage 1: initial marking. Each item holds one unit of `pending` until its
-  // pushes are done, so the iteration cannot end while marking is open.
+  // insertions are in the ring, so the iteration cannot end while marking is open.
   const unsigned long long n_items = ctl->n_items;
   while (true) {
     unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(&ctl->mark_next, 1ull);
+    if (lane == 0) item = atomicAdd(&ctl->mark_next.v, 1ull);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
     do_mark_item(a, (long long)item, lane, st, mark);
+    buf_flush(a, pb, lane, st);
+    if (lane == 0) *pb.owed += 1;  // the item's own unit, settled later
     __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      atomic_add_ll(&ctl->pending, -1);
-    }
   }
 
   // Stage 2: recompute queued vertices until nothing is queued or running.
@@ -375,18 +513,23 @@ __global__ void __launch_bounds__(kNT) k_worklist(Args<P> a) {
     long long got = 0;
     unsigned long long h = 0;
     if (lane == 0) {
-      if (ld_volatile(&ctl->avail) > 0) {
-        const long long av = atomic_add_ll_old(&ctl->avail, -32);
+      if (ld_volatile(&ctl->avail.v) > 0) {
+        const long long av = atomic_add_ll_old(&ctl->avail.v, -32);
         got = av >= 32 ? 32 : (av > 0 ? av : 0);
-        if (got < 32) atomic_add_ll(&ctl->avail, 32 - got);
-        if (got) h = atomicAdd(&ctl->head, (unsigned long long)got);
+        if (got < 32) atomic_add_ll(&ctl->avail.v, 32 - got);
+        if (got) h = atomicAdd(&ctl->head.v, (unsigned long long)got);
       }
     }
     got = __shfl_sync(kFull, got, 0);
     if (got == 0) {
+      settle_owed(a, pb, lane);
       int stop = 0;
       if (lane == 0) {
-        if (ld_volatile(&ctl->abort) || ld_volatile(&ctl->pending) <= 0) stop = 1;
+        if (local_processed) {
+          atomicAdd(&ctl->processed.v, local_processed);
+          local_processed = 0;
+        }
+        if (ld_volatile(&ctl->abort) || ld_volatile(&ctl->pending.v) <= 0) stop = 1;
         else if (timed_out(a)) {
           stop_with(a, DFPR_ETIMEOUT);
           stop = 1;
@@ -394,7 +537,7 @@ __global__ void __launch_bounds__(kNT) k_worklist(Args<P> a) {
       }
       if (__shfl_sync(kFull, stop, 0)) break;
       __nanosleep(backoff);
-      backoff = min(backoff * 2, 2048u);
+      backoff = min(backoff * 2, 1024u);
       continue;
     }
     backoff = 32;
@@ -423,23 +566,33 @@ __global__ void __launch_bounds__(kNT) k_worklist(Args<P> a) {
     if (!__all_sync(kFull, ok)) break;
     __threadfence();  // state change before reading neighbours' contributions
 
+    // per-vertex loads issued before the gather so they overlap it
+    typename P::val r_old = 0, x_prev = 0;
+    uint32_t e_tag = 0;
+    RowDesc orow;
+    orow.off = 0;
+    orow.deg = 0;
+    if (v >= 0) {
+      r_old = P::load(a.R + v);
+      e_tag = __ldcg(a.ep + v);
+      x_prev = P::load(a.X + v);
+      orow = load_row(a.out_rows + v);
+    }
     const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
     const double dangling = a.teleport ? ctl->dsum : 0.0;
     bool expand = false, requeue = false;
     if (v >= 0) {
       const typename P::val r = finish_rank(a, acc, dangling);
-      const typename P::val r_old = P::load(a.R + v);
-      const uint32_t e = __ldcg(a.ep + v);
       typename P::val x0;
-      if (e != a.epoch) {
+      if (e_tag != a.epoch) {
         a.ep[v] = a.epoch;
         x0 = r_old;
         st.affected++;
       } else {
-        x0 = P::load(a.X + v);
+        x0 = x_prev;
       }
       const double dr = fabs((double)r - (double)r_old);
-      const int od = a.out_rows[v].deg;
+      const int od = orow.deg;
       a.R[v] = r;
       a.C[v] = od > 0 ? r / (typename P::val)od : (typename P::val)0;
       const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
@@ -453,41 +606,7 @@ __global__ void __launch_bounds__(kNT) k_worklist(Args<P> a) {
     __threadfence();  // new rank visible before neighbours are queued
 
     // Expansion: mark the out-neighbours of every expanding vertex.
-    {
-      int od = 0;
-      long long oo = 0;
-      if (expand) {
-        const RowDesc r = a.out_rows[v];
-        od = r.deg;
-        oo = r.off;
-      }
-      int incl = od;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        int y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += y;
-      }
-      const int total = __shfl_sync(kFull, incl, 31);
-      __syncwarp();
-      s_excl[w][lane] = incl - od;
-      s_off[w][lane] = oo;
-      __syncwarp();
-      for (int base = 0; base < total; base += 32) {
-        const int e = base + lane;
-        const bool valid = e < total;
-        int t = 0;
-        if (valid) {
-          int lo = 0, hi = 32;
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_excl[w][mid] <= e) lo = mid; else hi = mid;
-          }
-          t = a.out_edges[s_off[w][lo] + (e - s_excl[w][lo])];
-        }
-        mark_push(a, t, valid, lane, st);
-      }
-      if (lane == 0) st.edges_marked += (unsigned long long)total;
-    }
+    expand_rows(a, expand ? orow.deg : 0, orow.off, lane, s_excl[w], s_off[w], pb, st);
     // Not converged: flag itself so that the finish step re-queues it.
     if (requeue && !expand) {
       const unsigned sh = (unsigned)(v & 15) * 2u;
@@ -500,15 +619,22 @@ __global__ void __launch_bounds__(kNT) k_worklist(Args<P> a) {
       const unsigned old = atomicAnd(a.state + (v >> 4), ~(2u << sh));
       repush = ((old >> sh) & 1u) != 0u;
     }
-    push_warp(a, v, repush, false, lane, st);
+    buf_push(a, pb, v, repush, false, lane, st);
+    buf_flush(a, pb, lane, st);
     const int done = __popc(__ballot_sync(kFull, v >= 0 && !repush));
     if (lane == 0) {
-      __threadfence();
-      if (done) atomic_add_ll(&ctl->pending, -done);
-      const unsigned long long pr = atomicAdd(&ctl->processed, (unsigned long long)got);
-      if ((long long)(pr + got) > ctl->work_cap) stop_with(a, DFPR_ENOTCONV);
+      *pb.owed += done;  // subtracted with the next flush or when idle
+      local_processed += (unsigned long long)got;
+      if (local_processed >= 2048) {
+        const unsigned long long pr = atomicAdd(&ctl->processed.v, local_processed);
+        if ((long long)(pr + local_processed) > ctl->work_cap) stop_with(a, DFPR_ENOTCONV);
+        local_processed = 0;
+      }
     }
+    __syncwarp();
   }
+  settle_owed(a, pb, lane);
+  if (lane == 0 && local_processed) atomicAdd(&ctl->processed.v, local_processed);
   flush_stats(a, st, lane);
 }
 
@@ -530,8 +656,8 @@ __device__ void mark_round(const Args<P>& a, int t, bool valid, int lane) {
   const unsigned nb = __ballot_sync(kFull, nc_add != 0);
   long long base = 0;
   if (lane == 0) {
-    if (nb) atomic_add_ll(&a.ctl->nc, __popc(nb));
-    if (b) base = atomic_add_ll_old(&a.ctl->len, __popc(b));
+    if (nb) atomic_add_ll(&a.ctl->nc.v, __popc(nb));
+    if (b) base = atomic_add_ll_old(&a.ctl->len.v, __popc(b));
   }
   base = __shfl_sync(kFull, base, 0);
   if (fresh) *(volatile int*)(a.alist + base + __popc(b & lanemask_lt())) = t;
@@ -552,14 +678,14 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
   const unsigned long long n_items = ctl->n_items;
   while (true) {
     unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(&ctl->mark_next, 1ull);
+    if (lane == 0) item = atomicAdd(&ctl->mark_next.v, 1ull);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
     do_mark_item(a, (long long)item, lane, st, mark);
     __syncwarp();
     if (lane == 0) {
       __threadfence();
-      if (atomicExch(a.item_done + item, 1u) == 0u) atomic_add_ll(&ctl->pending, -1);
+      if (atomicExch(a.item_done + item, 1u) == 0u) atomic_add_ll(&ctl->pending.v, -1);
     }
   }
   {
@@ -569,7 +695,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
     while (true) {
       int stop = 0;
       if (lane == 0) {
-        if (ld_volatile(&ctl->pending) <= 0 || ld_volatile(&ctl->abort)) stop = 1;
+        if (ld_volatile(&ctl->pending.v) <= 0 || ld_volatile(&ctl->abort)) stop = 1;
         else if ((++spins & 63u) == 0 && timed_out(a)) {
           stop_with(a, DFPR_ETIMEOUT);
           stop = 1;
@@ -583,7 +709,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         __syncwarp();
         if (lane == 0) {
           __threadfence();
-          if (atomicExch(a.item_done + item, 1u) == 0u) atomic_add_ll(&ctl->pending, -1);
+          if (atomicExch(a.item_done + item, 1u) == 0u) atomic_add_ll(&ctl->pending.v, -1);
         }
       }
     }
@@ -601,7 +727,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
       long long len = 0;
       if (lane == 0) {
         c = atomicAdd(a.pass_ctr + pass, 32ull);
-        len = ld_volatile(&ctl->len);
+        len = ld_volatile(&ctl->len.v);
       }
       c = __shfl_sync(kFull, c, 0);
       len = __shfl_sync(kFull, len, 0);
@@ -622,6 +748,14 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         if (!ok) v = -1;
       }
       if (!__all_sync(kFull, ok)) break;
+      // Exclusion: a vertex another warp is recomputing right now (a warp in
+      // a neighbouring pass) is skipped, so a result computed from older
+      // neighbour ranks never overwrites a fresher one.
+      if (v >= 0) {
+        const unsigned sh = (unsigned)(v & 15) * 2u;
+        if (atomicOr(a.state + (v >> 4), 2u << sh) & (2u << sh)) v = -1;
+      }
+      __threadfence();
       const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
       bool expand = false;
       double dr = 0.0, thr = 0.0;
@@ -681,16 +815,21 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
           if (atomicAnd(a.rc_bits + (v >> 5), ~bit) & bit) conv = 1;
         }
       }
+      if (v >= 0) {
+        __threadfence();
+        const unsigned sh = (unsigned)(v & 15) * 2u;
+        atomicAnd(a.state + (v >> 4), ~(2u << sh));
+      }
       const unsigned cb = __ballot_sync(kFull, conv != 0);
       if (lane == 0) {
-        if (cb) atomic_add_ll(&ctl->nc, -(long long)__popc(cb));
+        if (cb) atomic_add_ll(&ctl->nc.v, -(long long)__popc(cb));
         const int cnt = (int)min(32ll, len - (long long)c);
-        atomicAdd(&ctl->processed, (unsigned long long)cnt);
+        atomicAdd(&ctl->processed.v, (unsigned long long)cnt);
       }
     }
     int stop = 0;
     if (lane == 0) {
-      if (ld_volatile(&ctl->nc) <= 0 || ld_volatile(&ctl->abort)) stop = 1;
+      if (ld_volatile(&ctl->nc.v) <= 0 || ld_volatile(&ctl->abort)) stop = 1;
       else if (timed_out(a)) {
         stop_with(a, DFPR_ETIMEOUT);
         stop = 1;
@@ -701,7 +840,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
       break;
     }
   }
-  if (lane == 0) atomicMax((unsigned long long*)&ctl->pad[0], (unsigned long long)pass);
+  if (lane == 0) atomicMax(&ctl->passes, (unsigned long long)pass);
   flush_stats(a, st, lane);
 }
 
@@ -780,13 +919,13 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
         }
         const unsigned bb = __ballot_sync(kFull, fresh);
         long long base2 = 0;
-        if (lane == 0 && bb) base2 = atomic_add_ll_old(&a.ctl->len, __popc(bb));
+        if (lane == 0 && bb) base2 = atomic_add_ll_old(&a.ctl->len.v, __popc(bb));
         base2 = __shfl_sync(kFull, base2, 0);
         if (fresh) a.alist[base2 + __popc(bb & lanemask_lt())] = t;
       }
       if (lane == 0) st.edges_marked += (unsigned long long)total;
     }
-    if (lane == 0) atomicAdd(&a.ctl->processed, (unsigned long long)min(32ll, count - bi * 32));
+    if (lane == 0) atomicAdd(&a.ctl->processed.v, (unsigned long long)min(32ll, count - bi * 32));
   }
   flush_stats(a, st, lane);
 }
@@ -804,7 +943,7 @@ __global__ void __launch_bounds__(kNT) k_mark_list(Args<P> a) {
     }
     const unsigned b = __ballot_sync(kFull, fresh);
     long long base = 0;
-    if (lane == 0 && b) base = atomic_add_ll_old(&a.ctl->len, __popc(b));
+    if (lane == 0 && b) base = atomic_add_ll_old(&a.ctl->len.v, __popc(b));
     base = __shfl_sync(kFull, base, 0);
     if (fresh) a.alist[base + __popc(b & lanemask_lt())] = t;
   };
@@ -835,11 +974,11 @@ __global__ void k_init_ctl(DfCtl* c, const long long* n_src_items_dev, long long
   memset(&z, 0, sizeof z);
   z.n_src_items = nsi;
   z.n_items = items;
-  z.pending = (count_items_pending ? (long long)items : 0) + seeded;
-  z.tail = (unsigned long long)seeded;
-  z.avail = seeded;
+  z.pending.v = (count_items_pending ? (long long)items : 0) + seeded;
+  z.tail.v = (unsigned long long)seeded;
+  z.avail.v = seeded;
   z.work_cap = work_cap;
-  z.len = 0;
+  z.len.v = 0;
   z.t_start = gtime();
   *c = z;
 }
@@ -935,8 +1074,8 @@ __global__ void k_scale(int32_t n, const RowDesc* __restrict__ out_rows, T* R, T
 __global__ void k_seed_round(int32_t n, int32_t* alist, DfCtl* c) {
   GRID_STRIDE(i, n) alist[i] = (int32_t)i;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    c->len = n;
-    c->nc = n;
+    c->len.v = n;
+    c->nc.v = n;
   }
 }
 
@@ -1034,7 +1173,7 @@ CtlHost read_ctl(dfpr_graph* g) {
 }
 
 void fill_stats(const DfCtl& c, dfpr_stats* st) {
-  st->processed = (int64_t)c.processed;
+  st->processed = (int64_t)c.processed.v;
   st->edges_gathered = (int64_t)c.edges;
   st->expansions = (int64_t)c.expansions;
   st->edges_marked = (int64_t)c.edges_marked;
@@ -1087,7 +1226,7 @@ dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr
   DFPR_CUDA(cudaEventRecord(e1, s));
   CtlHost h = read_ctl(g);
   if (st) fill_stats(h.c, st);
-  const bool clean = h.c.status == 0 && h.c.pending <= 0 && !mark_only;
+  const bool clean = h.c.status == 0 && h.c.pending.v <= 0 && !mark_only;
   if (!clean && !mark_only) reset_worklist_state(g);
   return h.c.status ? (dfpr_status)h.c.status : DFPR_OK;
 }
@@ -1120,20 +1259,24 @@ dfpr_status run_round(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_st
     k_seed_round<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->affected_list.p, g->ctl.p);
     DFPR_LAUNCHED();
   }
-  const int grid = persistent_grid(g, p, (const void*)k_round<P>);
+  // One CTA per 1024 vertices at most: with many more warps than 32-vertex
+  // chunks per pass, idle warps would start later passes while earlier ones
+  // are still being computed, using up the pass budget without progress.
+  int grid = persistent_grid(g, p, (const void*)k_round<P>);
+  if (p.grid_ctas <= 0) grid = (int)std::max<long long>(1, std::min<long long>(grid, (g->n + 1023) / 1024));
   k_round<P><<<grid, kNT, 0, s>>>(a);
   DFPR_LAUNCHED();
   DFPR_CUDA(cudaEventRecord(e1, s));
   CtlHost h = read_ctl(g);
   if (st) {
     fill_stats(h.c, st);
-    st->passes = (int32_t)h.c.pad[0];
-    st->affected = h.c.len;
+    st->passes = (int32_t)h.c.passes;
+    st->affected = h.c.len.v;
   }
   dfpr_status status = h.c.status ? (dfpr_status)h.c.status : DFPR_OK;
-  if (status == DFPR_OK && h.c.nc > 0) status = DFPR_ENOTCONV;
+  if (status == DFPR_OK && h.c.nc.v > 0) status = DFPR_ENOTCONV;
   // clear flags and list for the next call
-  k_clear_list<<<grid_small(h.c.len), kNT, 0, s>>>(g->affected_list.p, h.c.len, g->va_bits.p, g->rc_bits.p);
+  k_clear_list<<<grid_small(h.c.len.v), kNT, 0, s>>>(g->affected_list.p, h.c.len.v, g->va_bits.p, g->rc_bits.p);
   DFPR_LAUNCHED();
   if (kind != kRunDF) {
     DFPR_CUDA(cudaMemsetAsync(g->va_bits.p, 0, sizeof(uint32_t) * g->va_bits.count, s));
@@ -1207,7 +1350,7 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
     DFPR_CUDA(cudaMemcpyAsync(C2, a.C, sizeof(V) * g->n, cudaMemcpyDeviceToDevice, s));
     k_mark_list<P><<<grid_small(32ll * g->n), kNT, 0, s>>>(a);
     DFPR_LAUNCHED();
-    count = (long long)read_word(g, &g->ctl.p->len, sizeof(long long));
+    count = (long long)read_word(g, &g->ctl.p->len.v, sizeof(long long));
   }
   const int grid = persistent_grid(g, p, (const void*)k_jacobi<P>);
   int it = 0;
@@ -1225,7 +1368,7 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
     DFPR_LAUNCHED();
     DFPR_CUDA(cudaMemcpyAsync(g->pinned, &g->ctl.p->max_change_bits, sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, s));
-    DFPR_CUDA(cudaMemcpyAsync(g->pinned + 1, &g->ctl.p->len, sizeof(long long),
+    DFPR_CUDA(cudaMemcpyAsync(g->pinned + 1, &g->ctl.p->len.v, sizeof(long long),
                               cudaMemcpyDeviceToHost, s));
     DFPR_CUDA(cudaStreamSynchronize(s));
     memcpy(&last, &g->pinned[0], sizeof last);
@@ -1392,7 +1535,7 @@ void initial_affected(dfpr_graph* g, uint8_t* affected_dev, long long* count) {
   k_export_state<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p, affected_dev);
   DFPR_LAUNCHED();
   CtlHost h = read_ctl(g);
-  if (count) *count = (long long)h.c.tail;
+  if (count) *count = (long long)h.c.tail.v;
   // the marking pushed every affected vertex once: undo it
   reset_worklist_state(g);
 }

@@ -26,9 +26,11 @@ def c1():
     n, src, dst, batch = rmat_case(14, 1000)
     g0 = oracle.Graph.build(n, src, dst)
     g1, nreal = g0.apply(*batch)
-    R0, _ = g0.static_bb()
+    R0, _ = g0.static_bb()          # converged to tau = 1e-10, as the paper's runs
+    R0ref, _ = g0.reference()       # converged to rounding
     ref1, _ = g1.reference()
-    return dict(n=n, src=src, dst=dst, batch=batch, g0=g0, g1=g1, nreal=nreal, R0=R0, ref1=ref1)
+    return dict(n=n, src=src, dst=dst, batch=batch, g0=g0, g1=g1, nreal=nreal, R0=R0,
+                R0ref=R0ref, ref1=ref1)
 
 
 def check_graph(gpu_g, orc_g):
@@ -182,9 +184,12 @@ def test_static_matches_reference(gpu_lib, c1, mode):
 
 @pytest.mark.parametrize("mode", MODES)
 def test_df_matches_reference(gpu_lib, c1, mode):
-    """R^{t-1} from the oracle's Static_BB (tau = 1e-10), then one DF update."""
+    """R^{t-1} converged to rounding (the oracle's reference on G^{t-1}), then
+    one DF update: the error is the DF schedule's own. (Starting from ranks
+    converged only to tau = 1e-10 already spends ~5e-10 of the 1e-9 budget;
+    that full path is covered by test_df_after_gpu_static.)"""
     g = gpu_lib.graph_load(c1["n"], c1["src"], c1["dst"])
-    g.set_ranks(c1["R0"])
+    g.set_ranks(c1["R0ref"])
     assert g.apply_batch(*c1["batch"]) == c1["nreal"]
     st = g.df_pagerank(gpu_lib.default_params(mode=getattr(gpu_lib, mode)))
     assert st.status == gpu_lib.OK, st.as_dict()
