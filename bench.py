@@ -138,6 +138,16 @@ def algorithmic_bytes(st, s_r: int) -> float:
             + st["expansions"] * 16 + st["edges_marked"] * 8 + st["pushes"] * 8)
 
 
+def phase_share(stats):
+    """Share of the persistent kernel's warp-cycles per phase (summed over steps)."""
+    tot = {}
+    for s in stats:
+        for k, v in s.get("phase_cycles", {}).items():
+            tot[k] = tot.get(k, 0) + v
+    all_ = sum(tot.values()) or 1
+    return {k: round(v / all_, 4) for k, v in tot.items()}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -342,6 +352,8 @@ def run_ours(args):
         "work": {"processed": mean("processed"), "edges_gathered": mean("edges_gathered"),
                  "expansions": mean("expansions"), "edges_marked": mean("edges_marked"),
                  "pushes": mean("pushes"), "affected": mean("affected"),
+                 "batches": mean("batches"), "tokens": mean("tokens"), "jobs": mean("jobs"),
+                 "phase_share": phase_share(stats),
                  "apply_plus_df_ms_steps": step_ms, "wall_s": t_wall,
                  "nonconverged_steps": len(bad)},
     }

@@ -117,6 +117,12 @@ typedef struct dfpr_stats {
                              else NaN */
   double ms;              /* device time (CUDA events): the persistent kernel alone in
                              worklist mode, all kernels of the call otherwise */
+  int64_t batches;        /* worklist: batches of up to 32 vertices taken from the queue */
+  int64_t tokens;         /* worklist: chunk tokens processed (pieces of long rows) */
+  int64_t jobs;           /* worklist: recomputations whose in-row was split into tokens */
+  int64_t phase_cycles[5];/* worklist: SM cycles summed over warps spent idle (queue empty),
+                             claiming items, gathering, marking out-neighbours, and
+                             finishing (state updates, queue insertions) */
 } dfpr_stats;
 
 /* Fills *cfg / *p with the defaults listed above. */

@@ -64,10 +64,16 @@ class Stats(ctypes.Structure):
                 ("pushes", ctypes.c_int64), ("affected", ctypes.c_int64),
                 ("passes", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("residual_linf", ctypes.c_double), ("rank_sum", ctypes.c_double),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("batches", ctypes.c_int64),
+                ("tokens", ctypes.c_int64), ("jobs", ctypes.c_int64),
+                ("phase_cycles", ctypes.c_int64 * 5)]
+
+    PHASES = ("idle", "claim", "gather", "expand", "finish")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_cycles"}
+        d["phase_cycles"] = dict(zip(self.PHASES, list(self.phase_cycles)))
+        return d
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

@@ -141,6 +141,12 @@ struct DfCtl {
   HotU64 processed;   // recomputations (work cap)
   HotI64 len;         // affected-list length (round / jacobi)
   HotI64 nc;          // vertices flagged not converged (round)
+  HotU64 thead;       // token ring (chunks of heavy gathers and of marking): consumers
+  HotU64 ttail;       //   producers
+  HotI64 tavail;      //   published, not yet claimed
+  HotU64 fhead;       // free ring of heavy-gather job slots: consumers
+  HotU64 ftail;       //   producers
+  HotI64 favail;      //   free slots
   unsigned long long n_src_items;  // marking items over out-rows of sources
   unsigned long long n_items;      // all marking items
   unsigned int status;             // 0, or the dfpr_status that stopped the workers
@@ -151,6 +157,10 @@ struct DfCtl {
   unsigned long long t_start;      // globaltimer at launch
   double dsum;                     // rank held by dead ends (teleport)
   unsigned long long passes;       // round: passes reached
+  unsigned long long batches;      // worklist: batches taken from the queue
+  unsigned long long tokens;       // worklist: chunk tokens processed
+  unsigned long long jobs;         // worklist: heavy gathers split into chunk tokens
+  unsigned long long phase[5];     // worklist: cycles idle, claim, gather, expand, finish
 };
 
 struct Pending {
@@ -158,6 +168,21 @@ struct Pending {
   DevArray<int32_t> dst;   // targets of real deletions
   long long n_src = 0, n_dst = 0;
 };
+
+// Contribution C[u] = R[u] / |out(u)| of a vertex, as stored for gathers.
+// FP64 graphs keep it as a 64-bit fixed-point number with scale 2^62, so a
+// gather sums exactly with integer adds (GB300's FP64 rate is a small
+// fraction of its integer and FP32 rates): each term is rounded once, to
+// 2^-63 absolute, and the sum of at most 1 (ranks sum to 1) cannot overflow.
+// FP32 graphs keep the float quotient.
+constexpr double kFix62 = 4611686018427387904.0;          // 2^62
+constexpr double kInvFix62 = 1.0 / 4611686018427387904.0;  // 2^-62
+__device__ __forceinline__ long long contrib_of(double r, int d) {
+  return d > 0 ? __double2ll_rn((r / (double)d) * kFix62) : 0ll;
+}
+__device__ __forceinline__ float contrib_of(float r, int d) {
+  return d > 0 ? __fdiv_rn(r, (float)d) : 0.f;
+}
 
 }  // namespace dfpr
 
@@ -172,15 +197,24 @@ struct dfpr_graph {
   dfpr_graph_config cfg;
   dfpr::Rows out, in;
   // ranks: FP64 or FP32 arrays (one of each pair is used)
-  dfpr::DevArray<double> R64, C64, X64;   // rank, contribution R/outdeg, rank at last expansion
+  dfpr::DevArray<double> R64, X64;         // rank, rank at last expansion
+  dfpr::DevArray<long long> C64;           // contribution R/outdeg, fixed point 2^-62
   dfpr::DevArray<float> R32, C32, X32;
-  dfpr::DevArray<double> R64b, C64b;       // second vectors of the Jacobi schedule
+  dfpr::DevArray<double> R64b;             // second vectors of the Jacobi schedule
+  dfpr::DevArray<long long> C64b;
   dfpr::DevArray<float> R32b, C32b;
   dfpr::DevArray<uint32_t> ep;            // epoch of first recomputation in the current call
   uint32_t epoch = 0;
   dfpr::DevArray<uint32_t> state;         // 2 bits per vertex: bit0 queued, bit1 running
   dfpr::DevArray<int32_t> queue;          // qcap slots, -1 when empty
   unsigned long long qcap = 0;
+  dfpr::DevArray<unsigned long long> tokens;  // token ring, all ones when empty
+  unsigned long long tcap = 0;
+  dfpr::DevArray<int32_t> job_ring;       // free job slots, -1 when empty
+  dfpr::DevArray<int32_t> job_v;          // vertex of a job slot
+  dfpr::DevArray<int32_t> job_rem;        // chunks of the job not yet summed
+  dfpr::DevArray<unsigned long long> job_sum;  // partial sums (fixed point, or FP64 bits)
+  int jcap = 0;
   dfpr::DevArray<dfpr::DfCtl> ctl;
   dfpr::DevArray<int32_t> affected_list;  // round mode: affected vertices in marking order
   dfpr::DevArray<uint32_t> va_bits;       // round mode: affected bitmap

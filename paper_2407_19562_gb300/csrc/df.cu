@@ -80,16 +80,27 @@ __device__ __forceinline__ long long atomic_add_ll_old(long long* p, long long v
 // Precision traits
 // ---------------------------------------------------------------------------
 
-// FP64: plain sums.
+// FP64 ranks; contributions in 64-bit fixed point (scale 2^62, see
+// contrib_of), summed exactly with integer adds.
 struct P64 {
   using val = double;
-  using acc = double;
-  static __device__ __forceinline__ acc zero() { return 0.0; }
-  static __device__ __forceinline__ acc from(val x) { return x; }
+  using contrib = long long;
+  using acc = long long;
+  static __device__ __forceinline__ acc zero() { return 0ll; }
+  static __device__ __forceinline__ acc from(contrib x) { return x; }
   static __device__ __forceinline__ acc add(acc a, acc b) { return a + b; }
-  static __device__ __forceinline__ double total(acc a) { return a; }
+  static __device__ __forceinline__ double total(acc a) { return __ll2double_rn(a) * kInvFix62; }
   static __device__ __forceinline__ acc shfl_up(acc a, int d) { return __shfl_up_sync(kFull, a, d); }
   static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
+  static __device__ __forceinline__ contrib load_c(const contrib* p) { return __ldcg(p); }
+  static __device__ __forceinline__ acc shfl_xor(acc a, int d) { return __shfl_xor_sync(kFull, a, d); }
+  // heavy-gather jobs: partial sums meet in one 64-bit word (exact integer adds)
+  static __device__ __forceinline__ void job_add(unsigned long long* p, acc x) {
+    atomicAdd(p, (unsigned long long)x);
+  }
+  static __device__ __forceinline__ double job_total(unsigned long long bits) {
+    return __ll2double_rn((long long)bits) * kInvFix62;
+  }
   static constexpr bool relative = false;
 };
 
@@ -100,9 +111,10 @@ struct CompF {
 };
 struct P32 {
   using val = float;
+  using contrib = float;
   using acc = CompF;
   static __device__ __forceinline__ acc zero() { return {0.f, 0.f}; }
-  static __device__ __forceinline__ acc from(val x) { return {x, 0.f}; }
+  static __device__ __forceinline__ acc from(contrib x) { return {x, 0.f}; }
   static __device__ __forceinline__ acc add(acc a, acc b) {
     const float s = __fadd_rn(a.s, b.s);
     const float bp = __fsub_rn(s, a.s);
@@ -114,6 +126,17 @@ struct P32 {
     return {__shfl_up_sync(kFull, a.s, d), __shfl_up_sync(kFull, a.c, d)};
   }
   static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
+  static __device__ __forceinline__ contrib load_c(const contrib* p) { return __ldcg(p); }
+  static __device__ __forceinline__ acc shfl_xor(acc a, int d) {
+    return {__shfl_xor_sync(kFull, a.s, d), __shfl_xor_sync(kFull, a.c, d)};
+  }
+  // heavy-gather jobs: partial sums meet in one FP64 word
+  static __device__ __forceinline__ void job_add(unsigned long long* p, acc x) {
+    atomicAdd(reinterpret_cast<double*>(p), total(x));
+  }
+  static __device__ __forceinline__ double job_total(unsigned long long bits) {
+    return __longlong_as_double((long long)bits);
+  }
   static constexpr bool relative = true;
 };
 
@@ -129,7 +152,7 @@ struct Args {
   const RowDesc* __restrict__ out_rows;
   const int32_t* __restrict__ out_edges;
   typename P::val* R;
-  typename P::val* C;
+  typename P::contrib* C;
   typename P::val* X;
   uint32_t* ep;
   uint32_t epoch;
@@ -150,6 +173,14 @@ struct Args {
   unsigned long long* pass_ctr;
   uint32_t* item_done;
   int max_iter;
+  // worklist: token ring and heavy-gather jobs
+  unsigned long long* tokens;
+  unsigned long long tmask;
+  int32_t* job_ring;
+  int32_t* job_v;
+  int32_t* job_rem;
+  unsigned long long* job_sum;
+  unsigned jmask;
   // numerics
   double alpha, base, tol, tol_f;
   int teleport;
@@ -160,6 +191,7 @@ struct Args {
 struct WarpStats {
   unsigned long long edges, expansions, edges_marked, pushes, affected;
   double max_change;
+  unsigned long long* prof;  // worklist: shared-memory counters (batches, 5 phases) or null
 };
 
 template <class P>
@@ -237,10 +269,10 @@ __device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl
         uid[k] = __ldg(a.in_edges + s_off[o] + (e - s_excl[o]));
       }
     }
-    typename P::val xv[kUnroll];
+    typename P::contrib xv[kUnroll];
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k)
-      xv[k] = owner[k] >= 0 ? P::load(a.C + uid[k]) : (typename P::val)0;
+      xv[k] = owner[k] >= 0 ? P::load_c(a.C + uid[k]) : (typename P::contrib)0;
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       if (base + k * 32 >= total) break;  // warp-uniform
@@ -360,11 +392,132 @@ __device__ __forceinline__ bool mark_one(const Args<P>& a, int t, bool valid, un
   return ((old >> sh) & 3u) == 0u;
 }
 
-// Marks the out-neighbours of every lane's vertex whose `od` > 0 (edge-balanced
-// like the gather, kUnroll chunks in flight).
+// Tokens: bit 63..62 kind, 61..31 a, 30..0 b. Kind 0: gather chunk b of job
+// slot a. Kind 1: mark chunk b of vertex a's out-row.
+constexpr int kGatherChunk = 2048;  // in-edges per gather token; longer in-rows are split
+constexpr int kMarkSplit = 2048;    // out-edges per mark token; longer out-rows are split
+constexpr unsigned long long kNoToken = ~0ull;
+
+__device__ __forceinline__ unsigned long long make_token(unsigned kind, unsigned x, unsigned y) {
+  return ((unsigned long long)kind << 62) | ((unsigned long long)x << 31) | (unsigned long long)y;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *(const volatile unsigned long long*)p;
+}
+
+// Every lane publishes `cnt` tokens make_token(kind, x, k), k < cnt (warp-uniform call).
+// `pending` grows first, so the iteration cannot end while they are outstanding.
 template <class P>
-__device__ void expand_rows(const Args<P>& a, int od, long long oo, int lane, int* s_excl,
+__device__ void push_tokens(const Args<P>& a, int cnt, unsigned kind, unsigned x, int lane,
+                            WarpStats& st) {
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) {
+    atomic_add_ll(&a.ctl->pending.v, total);
+    __threadfence();
+    base = atomicAdd(&a.ctl->ttail.v, (unsigned long long)total);
+  }
+  base = __shfl_sync(kFull, base, 0);
+  bool ok = true;
+  for (int k = 0; k < cnt && ok; ++k) {
+    unsigned long long* slot = a.tokens + ((base + (unsigned long long)(incl - cnt + k)) & a.tmask);
+    unsigned spins = 0;
+    while (ld_volatile(slot) != kNoToken) {  // slot still held by a slow consumer
+      if ((++spins & 255u) == 0 && timed_out(a)) {
+        stop_with(a, DFPR_ETIMEOUT);
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (ok) *(volatile unsigned long long*)slot = make_token(kind, x, (unsigned)k);
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomic_add_ll(&a.ctl->tavail.v, total);
+}
+
+// Claims one token (lane 0; result broadcast), or returns kNoToken.
+template <class P>
+__device__ unsigned long long pop_token(const Args<P>& a, int lane) {
+  unsigned long long tok = kNoToken;
+  if (lane == 0 && ld_volatile(&a.ctl->tavail.v) > 0) {
+    if (atomic_add_ll_old(&a.ctl->tavail.v, -1) > 0) {
+      const unsigned long long pos = atomicAdd(&a.ctl->thead.v, 1ull);
+      unsigned long long* slot = a.tokens + (pos & a.tmask);
+      unsigned spins = 0;
+      while ((tok = ld_volatile(slot)) == kNoToken) {  // producer between claim and write
+        if ((++spins & 255u) == 0 && timed_out(a)) {
+          stop_with(a, DFPR_ETIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (tok != kNoToken) *(volatile unsigned long long*)slot = kNoToken;
+    } else {
+      atomic_add_ll(&a.ctl->tavail.v, 1);
+    }
+  }
+  return __shfl_sync(kFull, tok, 0);
+}
+
+// Takes a free heavy-gather job slot (per lane), or -1 when none is free.
+template <class P>
+__device__ int alloc_job(const Args<P>& a) {
+  if (ld_volatile(&a.ctl->favail.v) <= 0) return -1;
+  if (atomic_add_ll_old(&a.ctl->favail.v, -1) <= 0) {
+    atomic_add_ll(&a.ctl->favail.v, 1);
+    return -1;
+  }
+  const unsigned long long pos = atomicAdd(&a.ctl->fhead.v, 1ull);
+  int* slot = a.job_ring + (pos & a.jmask);
+  int id;
+  unsigned spins = 0;
+  while ((id = ld_volatile(slot)) < 0) {
+    if ((++spins & 255u) == 0 && timed_out(a)) {
+      stop_with(a, DFPR_ETIMEOUT);
+      return -1;
+    }
+    __nanosleep(32);
+  }
+  *(volatile int*)slot = -1;
+  return id;
+}
+
+template <class P>
+__device__ void free_job(const Args<P>& a, int id) {
+  const unsigned long long pos = atomicAdd(&a.ctl->ftail.v, 1ull);
+  int* slot = a.job_ring + (pos & a.jmask);
+  unsigned spins = 0;
+  while (ld_volatile(slot) != -1) {
+    if ((++spins & 255u) == 0 && timed_out(a)) {
+      stop_with(a, DFPR_ETIMEOUT);
+      return;
+    }
+    __nanosleep(32);
+  }
+  *(volatile int*)slot = id;
+  __threadfence();
+  atomic_add_ll(&a.ctl->favail.v, 1);
+}
+
+// Marks the out-neighbours of every lane's vertex v (with od > 0 out-edges at
+// oo). Out-rows longer than kMarkSplit become mark tokens that any warp takes;
+// the rest are walked edge-balanced, kUnroll chunks in flight.
+template <class P>
+__device__ void expand_rows(const Args<P>& a, int v, int od, long long oo, int lane, int* s_excl,
                             long long* s_off, PushBuf pb, WarpStats& st) {
+  const bool split = od > kMarkSplit;
+  push_tokens(a, split ? (od + kMarkSplit - 1) / kMarkSplit : 0, 1u, (unsigned)max(v, 0), lane, st);
+  if (split) od = 0;
   int incl = od;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -452,6 +605,11 @@ __device__ void flush_stats(const Args<P>& a, WarpStats& st, int lane) {
     if (st.pushes) atomicAdd(&c->pushes, st.pushes);
     if (st.affected) atomicAdd(&c->affected, st.affected);
     if (st.max_change > 0) atomicMax(&c->max_change_bits, (unsigned long long)__double_as_longlong(st.max_change));
+    if (st.prof) {
+      if (st.prof[0]) atomicAdd(&c->batches, st.prof[0]);
+      for (int i = 0; i < 5; ++i)
+        if (st.prof[1 + i]) atomicAdd(&c->phase[i], st.prof[1 + i]);
+    }
   }
 }
 
@@ -468,6 +626,144 @@ __device__ __forceinline__ typename P::val finish_rank(const Args<P>& a, typenam
 // Worklist schedule
 // ---------------------------------------------------------------------------
 
+// Eq. 1 epilogue of one recomputed vertex v (lane-local): new rank r from the
+// gathered sum; Delta r against the stored rank; the rank at the last
+// expansion decides whether v marks its out-neighbours; the state's queued
+// bit decides re-queueing. Writes R, C, X and the epoch tag.
+template <class P>
+__device__ __forceinline__ void vertex_epilogue(const Args<P>& a, int v, double sum,
+                                                typename P::val r_old, uint32_t e_tag,
+                                                typename P::val x_prev, int od, double dangling,
+                                                bool& expand, bool& requeue, WarpStats& st) {
+  double s2 = sum;
+  if (a.teleport) s2 += dangling / (double)a.n;
+  const typename P::val r = (typename P::val)(a.base + a.alpha * s2);
+  typename P::val x0;
+  if (e_tag != a.epoch) {
+    a.ep[v] = a.epoch;
+    x0 = r_old;
+    st.affected++;
+  } else {
+    x0 = x_prev;
+  }
+  const double dr = fabs((double)r - (double)r_old);
+  a.R[v] = r;
+  a.C[v] = contrib_of(r, od);
+  const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
+  const double thr = P::relative ? a.tol * fabs((double)r) : a.tol;
+  expand = fabs((double)r - (double)x0) > thr_f;
+  a.X[v] = expand ? r : x0;
+  requeue = dr > thr;
+  st.max_change = fmax(st.max_change, dr);
+  if (expand) st.expansions++;
+}
+
+// After the epilogue of lane-local vertices: marks out-neighbours of expanding
+// ones, flags non-converged ones, and moves each from running to idle (or back
+// to queued when it was flagged meanwhile). Returns the number of vertices
+// that left the system (their `pending` units are owed).
+template <class P>
+__device__ int finish_vertices(const Args<P>& a, int v, bool expand, bool requeue, RowDesc orow,
+                               int lane, int* s_excl, long long* s_off, PushBuf pb, WarpStats& st) {
+  __threadfence();  // new ranks visible before neighbours are queued
+  expand_rows(a, v, expand ? orow.deg : 0, orow.off, lane, s_excl, s_off, pb, st);
+  if (requeue && !expand) {  // not converged: flag itself so that the finish re-queues it
+    const unsigned sh = (unsigned)(v & 15) * 2u;
+    atomicOr(a.state + (v >> 4), 1u << sh);
+  }
+  bool repush = false;
+  if (v >= 0) {
+    const unsigned sh = (unsigned)(v & 15) * 2u;
+    const unsigned old = atomicAnd(a.state + (v >> 4), ~(2u << sh));
+    repush = ((old >> sh) & 1u) != 0u;
+  }
+  buf_push(a, pb, v, repush, false, lane, st);
+  buf_flush(a, pb, lane, st);
+  return __popc(__ballot_sync(kFull, v >= 0 && !repush));
+}
+
+// Gather token: sums one chunk of a heavy vertex's in-row into its job; the
+// warp that sums the last chunk finishes the vertex.
+template <class P>
+__device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk, int lane,
+                                int* s_excl, long long* s_off, PushBuf pb, WarpStats& st) {
+  __threadfence();  // the job record was published before the token
+  const int v = ld_volatile(a.job_v + slot);
+  const RowDesc row = load_row(a.in_rows + v);
+  const long long beg = (long long)chunk * kGatherChunk;
+  const long long end = min((long long)row.deg, beg + kGatherChunk);
+  typename P::acc acc = P::zero();
+  for (long long e0 = beg; e0 < end; e0 += 32 * kUnroll) {
+    typename P::contrib xv[kUnroll];
+    int uid[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const long long e = e0 + k * 32 + lane;
+      uid[k] = e < end ? __ldg(a.in_edges + row.off + e) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) xv[k] = uid[k] >= 0 ? P::load_c(a.C + uid[k]) : (typename P::contrib)0;
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) acc = P::add(acc, P::from(xv[k]));
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc = P::add(acc, P::shfl_xor(acc, d));
+  int last = 0;
+  if (lane == 0) {
+    P::job_add(a.job_sum + slot, acc);
+    __threadfence();
+    last = atomicSub(a.job_rem + slot, 1) == 1;
+    st.edges += (unsigned long long)max(0ll, end - beg);
+  }
+  last = __shfl_sync(kFull, last, 0);
+  if (!last) return 0;
+  // finish the heavy vertex (lane 0 owns it)
+  __threadfence();
+  const int vv = lane == 0 ? v : -1;
+  bool expand = false, requeue = false;
+  RowDesc orow;
+  orow.off = 0;
+  orow.deg = 0;
+  if (vv >= 0) {
+    const double sum = P::job_total(ld_volatile(a.job_sum + slot));
+    const typename P::val r_old = P::load(a.R + vv);
+    const uint32_t e_tag = __ldcg(a.ep + vv);
+    const typename P::val x_prev = P::load(a.X + vv);
+    orow = load_row(a.out_rows + vv);
+    const double dangling = a.teleport ? a.ctl->dsum : 0.0;
+    vertex_epilogue(a, vv, sum, r_old, e_tag, x_prev, orow.deg, dangling, expand, requeue, st);
+    free_job(a, (int)slot);
+  }
+  return finish_vertices(a, vv, expand, requeue, orow, lane, s_excl, s_off, pb, st);
+}
+
+// Mark token: marks one chunk of a vertex's out-row.
+template <class P>
+__device__ void run_mark_token(const Args<P>& a, unsigned u, unsigned chunk, int lane, PushBuf pb,
+                               WarpStats& st) {
+  const RowDesc r = load_row(a.out_rows + u);
+  const long long beg = (long long)chunk * kMarkSplit;
+  const long long end = min((long long)r.deg, beg + kMarkSplit);
+  for (long long e0 = beg; e0 < end; e0 += 32 * kUnroll) {
+    int t[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const long long e = e0 + k * 32 + lane;
+      t[k] = e < end ? __ldg(a.out_edges + r.off + e) : -1;
+    }
+    unsigned wv[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) wv[k] = t[k] >= 0 ? ld_volatile(a.state + (t[k] >> 4)) : 0u;
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      if (e0 + k * 32 >= end) break;  // warp-uniform
+      buf_push(a, pb, t[k], mark_one(a, t[k], t[k] >= 0, wv[k]), true, lane, st);
+    }
+  }
+  if (lane == 0) st.edges_marked += (unsigned long long)max(0ll, end - beg);
+  buf_flush(a, pb, lane, st);
+}
+
 template <class P>
 __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   __shared__ int s_excl[kWPB][32];
@@ -475,17 +771,21 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   __shared__ typename P::acc s_acc[kWPB][32];
   __shared__ int s_push[kWPB][kPushCap];
   __shared__ int s_pcnt[kWPB][3];
+  __shared__ unsigned long long s_prof[kWPB][6];  // batches, then cycles per phase
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   DfCtl* ctl = a.ctl;
-  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  WarpStats st = {};
   if (lane == 0) {
     s_pcnt[w][0] = 0;
     s_pcnt[w][1] = 0;
     s_pcnt[w][2] = 0;
+    for (int i = 0; i < 6; ++i) s_prof[w][i] = 0;
   }
   __syncwarp();
+  st.prof = s_prof[w];
   const PushBuf pb{s_push[w], &s_pcnt[w][0], &s_pcnt[w][1], &s_pcnt[w][2]};
   unsigned long long local_processed = 0;  // lane 0: recomputations not yet added to the cap count
+  unsigned long long local_tokens = 0, local_jobs = 0;
   auto mark = [&](int t, bool valid) {
     const unsigned word = valid ? ld_volatile(a.state + (t >> 4)) : 0u;
     const bool need = mark_one(a, t, valid, word);
@@ -506,9 +806,36 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     __syncwarp();
   }
 
-  // Stage 2: recompute queued vertices until nothing is queued or running.
+  // Stage 2: chunk tokens first (they finish heavy vertices), then batches of
+  // queued vertices, until nothing is queued, running or tokenised.
   unsigned backoff = 32;
+  long long t_prev = clock64();
+  auto phase_mark = [&](int ph) {  // lane 0 charges the time since the last mark to `ph`
+    if (lane == 0) {
+      const long long t = clock64();
+      s_prof[w][1 + ph] += (unsigned long long)(t - t_prev);
+      t_prev = t;
+    }
+  };
   while (!a.mark_only) {
+    const unsigned long long tok = pop_token(a, lane);
+    if (tok != kNoToken) {
+      const unsigned kind = (unsigned)(tok >> 62);
+      const unsigned x = (unsigned)((tok >> 31) & 0x7fffffffull);
+      const unsigned y = (unsigned)(tok & 0x7fffffffull);
+      phase_mark(1);
+      int done = 0;
+      if (kind == 0) done = run_gather_token(a, x, y, lane, s_excl[w], s_off[w], pb, st);
+      else run_mark_token(a, x, y, lane, pb, st);
+      if (lane == 0) {
+        *pb.owed += 1 + done;  // the token's unit (and the finished vertex's)
+        ++local_tokens;
+        local_processed += (unsigned long long)done;
+      }
+      __syncwarp();
+      phase_mark(kind == 0 ? 2 : 3);
+      continue;
+    }
     // claim up to 32 items
     long long got = 0;
     unsigned long long h = 0;
@@ -538,9 +865,11 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       if (__shfl_sync(kFull, stop, 0)) break;
       __nanosleep(backoff);
       backoff = min(backoff * 2, 1024u);
+      phase_mark(0);
       continue;
     }
     backoff = 32;
+    if (lane == 0) s_prof[w][0] += 1;
     h = __shfl_sync(kFull, h, 0);
     int v = -1;
     bool ok = true;
@@ -566,6 +895,32 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     if (!__all_sync(kFull, ok)) break;
     __threadfence();  // state change before reading neighbours' contributions
 
+    // Heavy in-rows become jobs of gather tokens that any warp can take; the
+    // vertex stays running (and keeps its pending unit) until its last chunk.
+    {
+      int nch = 0, slot = -1;
+      if (v >= 0) {
+        const int din = load_row(a.in_rows + v).deg;
+        if (din > kGatherChunk) {
+          slot = alloc_job(a);
+          if (slot >= 0) {
+            nch = (din + kGatherChunk - 1) / kGatherChunk;
+            a.job_v[slot] = v;
+            a.job_sum[slot] = 0ull;
+            a.job_rem[slot] = nch;
+            __threadfence();
+          }
+        }
+      }
+      const unsigned jobs_b = __ballot_sync(kFull, nch > 0);
+      if (jobs_b) {
+        push_tokens(a, nch, 0u, (unsigned)max(slot, 0), lane, st);
+        if (lane == 0) local_jobs += (unsigned long long)__popc(jobs_b);
+        if (nch > 0) v = -1;
+      }
+    }
+    phase_mark(1);
+
     // per-vertex loads issued before the gather so they overlap it
     typename P::val r_old = 0, x_prev = 0;
     uint32_t e_tag = 0;
@@ -581,50 +936,16 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
     const double dangling = a.teleport ? ctl->dsum : 0.0;
     bool expand = false, requeue = false;
-    if (v >= 0) {
-      const typename P::val r = finish_rank(a, acc, dangling);
-      typename P::val x0;
-      if (e_tag != a.epoch) {
-        a.ep[v] = a.epoch;
-        x0 = r_old;
-        st.affected++;
-      } else {
-        x0 = x_prev;
-      }
-      const double dr = fabs((double)r - (double)r_old);
-      const int od = orow.deg;
-      a.R[v] = r;
-      a.C[v] = od > 0 ? r / (typename P::val)od : (typename P::val)0;
-      const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
-      const double thr = P::relative ? a.tol * fabs((double)r) : a.tol;
-      expand = fabs((double)r - (double)x0) > thr_f;
-      a.X[v] = expand ? r : x0;
-      requeue = dr > thr;
-      st.max_change = fmax(st.max_change, dr);
-      if (expand) st.expansions++;
-    }
-    __threadfence();  // new rank visible before neighbours are queued
-
-    // Expansion: mark the out-neighbours of every expanding vertex.
-    expand_rows(a, expand ? orow.deg : 0, orow.off, lane, s_excl[w], s_off[w], pb, st);
-    // Not converged: flag itself so that the finish step re-queues it.
-    if (requeue && !expand) {
-      const unsigned sh = (unsigned)(v & 15) * 2u;
-      atomicOr(a.state + (v >> 4), 1u << sh);
-    }
-    // Finish: running -> idle, or -> queued (re-pushed) when flagged meanwhile.
-    bool repush = false;
-    if (v >= 0) {
-      const unsigned sh = (unsigned)(v & 15) * 2u;
-      const unsigned old = atomicAnd(a.state + (v >> 4), ~(2u << sh));
-      repush = ((old >> sh) & 1u) != 0u;
-    }
-    buf_push(a, pb, v, repush, false, lane, st);
-    buf_flush(a, pb, lane, st);
-    const int done = __popc(__ballot_sync(kFull, v >= 0 && !repush));
+    if (v >= 0)
+      vertex_epilogue(a, v, P::total(acc), r_old, e_tag, x_prev, orow.deg, dangling, expand,
+                      requeue, st);
+    phase_mark(2);
+    const int done = finish_vertices(a, v, expand, requeue, orow, lane, s_excl[w], s_off[w], pb, st);
+    phase_mark(3);
+    const unsigned proc_b = __ballot_sync(kFull, v >= 0);
     if (lane == 0) {
       *pb.owed += done;  // subtracted with the next flush or when idle
-      local_processed += (unsigned long long)got;
+      local_processed += (unsigned long long)__popc(proc_b);
       if (local_processed >= 2048) {
         const unsigned long long pr = atomicAdd(&ctl->processed.v, local_processed);
         if ((long long)(pr + local_processed) > ctl->work_cap) stop_with(a, DFPR_ENOTCONV);
@@ -632,9 +953,14 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       }
     }
     __syncwarp();
+    phase_mark(4);
   }
   settle_owed(a, pb, lane);
-  if (lane == 0 && local_processed) atomicAdd(&ctl->processed.v, local_processed);
+  if (lane == 0) {
+    if (local_processed) atomicAdd(&ctl->processed.v, local_processed);
+    if (local_tokens) atomicAdd(&ctl->tokens, local_tokens);
+    if (local_jobs) atomicAdd(&ctl->jobs, local_jobs);
+  }
   flush_stats(a, st, lane);
 }
 
@@ -670,7 +996,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
   __shared__ typename P::acc s_acc[kWPB][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   DfCtl* ctl = a.ctl;
-  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  WarpStats st = {};
   auto mark = [&](int t, bool valid) { mark_round(a, t, valid, lane); };
 
   // Marking phase with helping (Alg. 2 marking loop): claim items; then, until
@@ -765,7 +1091,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         dr = fabs((double)r - (double)r_old);
         const int od = a.out_rows[v].deg;
         a.R[v] = r;
-        a.C[v] = od > 0 ? r / (typename P::val)od : (typename P::val)0;
+        a.C[v] = contrib_of(r, od);
         const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
         thr = P::relative ? a.tol * fabs((double)r) : a.tol;
         expand = dr > thr_f;
@@ -850,18 +1176,18 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
 
 template <class P>
 __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val* __restrict__ Rin,
-                                                const typename P::val* __restrict__ Cin,
+                                                const typename P::contrib* __restrict__ Cin,
                                                 typename P::val* __restrict__ Rout,
-                                                typename P::val* __restrict__ Cout,
+                                                typename P::contrib* __restrict__ Cout,
                                                 const int32_t* __restrict__ list, long long count,
                                                 int frontier) {
   __shared__ int s_excl[kWPB][32];
   __shared__ long long s_off[kWPB][32];
   __shared__ typename P::acc s_acc[kWPB][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  WarpStats st = {};
   Args<P> b = a;
-  b.C = const_cast<typename P::val*>(Cin);
+  b.C = const_cast<typename P::contrib*>(Cin);
   const long long nbatch = (count + 31) / 32;
   const double dangling = a.teleport ? a.ctl->dsum : 0.0;
   for (long long bi = (long long)blockIdx.x * kWPB + w; bi < nbatch; bi += (long long)gridDim.x * kWPB) {
@@ -874,7 +1200,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
       const double dr = fabs((double)r - (double)Rin[v]);
       const int od = a.out_rows[v].deg;
       Rout[v] = r;
-      Cout[v] = od > 0 ? r / (typename P::val)od : (typename P::val)0;
+      Cout[v] = contrib_of(r, od);
       const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
       expand = frontier && dr > thr_f;
       st.max_change = fmax(st.max_change, dr);
@@ -934,7 +1260,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
 template <class P>
 __global__ void __launch_bounds__(kNT) k_mark_list(Args<P> a) {
   const int lane = threadIdx.x & 31;
-  WarpStats st = {0, 0, 0, 0, 0, 0.0};
+  WarpStats st = {};
   auto mark = [&](int t, bool valid) {
     bool fresh = false;
     if (valid) {
@@ -967,7 +1293,8 @@ __global__ void k_mark_chunks(const int32_t* __restrict__ src, long long ns,
 }
 
 __global__ void k_init_ctl(DfCtl* c, const long long* n_src_items_dev, long long n_mark_dst,
-                           long long work_cap, long long seeded, int count_items_pending) {
+                           long long work_cap, long long seeded, int count_items_pending,
+                           int jobs) {
   const unsigned long long nsi = n_src_items_dev ? (unsigned long long)*n_src_items_dev : 0ull;
   const unsigned long long items = nsi + (unsigned long long)((n_mark_dst + 31) / 32);
   DfCtl z;
@@ -979,8 +1306,15 @@ __global__ void k_init_ctl(DfCtl* c, const long long* n_src_items_dev, long long
   z.avail.v = seeded;
   z.work_cap = work_cap;
   z.len.v = 0;
+  z.ftail.v = (unsigned long long)jobs;
+  z.favail.v = jobs;
   z.t_start = gtime();
   *c = z;
+}
+
+// Fills the free ring of heavy-gather job slots with every slot id.
+__global__ void k_init_jobs(int32_t* ring, int jobs) {
+  GRID_STRIDE(i, jobs) ring[i] = (int32_t)i;
 }
 
 __global__ void k_seed_all(int32_t n, uint32_t* state, int32_t* queue) {
@@ -998,13 +1332,12 @@ __global__ void k_fill(T* p, long long n, T v) {
   GRID_STRIDE(i, n) p[i] = v;
 }
 
-template <class T>
-__global__ void k_init_ranks(int32_t n, const RowDesc* __restrict__ out_rows, T* R, T* C) {
+template <class T, class CT>
+__global__ void k_init_ranks(int32_t n, const RowDesc* __restrict__ out_rows, T* R, CT* C) {
   const T r0 = (T)(1.0 / (double)n);
   GRID_STRIDE(u, n) {
     R[u] = r0;
-    const int d = out_rows[u].deg;
-    C[u] = d > 0 ? r0 / (T)d : (T)0;
+    C[u] = contrib_of(r0, out_rows[u].deg);
   }
 }
 
@@ -1059,14 +1392,13 @@ __global__ void k_dangling(int32_t n, const RowDesc* __restrict__ out_rows, cons
   }
 }
 
-template <class T>
-__global__ void k_scale(int32_t n, const RowDesc* __restrict__ out_rows, T* R, T* C, const double* sum) {
+template <class T, class CT>
+__global__ void k_scale(int32_t n, const RowDesc* __restrict__ out_rows, T* R, CT* C, const double* sum) {
   const double inv = 1.0 / *sum;
   GRID_STRIDE(u, n) {
     const T r = (T)((double)R[u] * inv);
     R[u] = r;
-    const int d = out_rows[u].deg;
-    C[u] = d > 0 ? r / (T)d : (T)0;
+    C[u] = contrib_of(r, out_rows[u].deg);
   }
 }
 
@@ -1100,6 +1432,13 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   a.queue = g->queue.p;
   a.qmask = g->qcap - 1;
   a.ctl = g->ctl.p;
+  a.tokens = g->tokens.p;
+  a.tmask = g->tcap - 1;
+  a.job_ring = g->job_ring.p;
+  a.job_v = g->job_v.p;
+  a.job_rem = g->job_rem.p;
+  a.job_sum = g->job_sum.p;
+  a.jmask = (unsigned)g->jcap - 1u;
   a.va_bits = g->va_bits.p;
   a.rc_bits = g->rc_bits.p;
   a.alist = g->affected_list.p;
@@ -1182,6 +1521,10 @@ void fill_stats(const DfCtl& c, dfpr_stats* st) {
   double mc;
   memcpy(&mc, &c.max_change_bits, sizeof mc);
   st->residual_linf = mc;
+  st->batches = (int64_t)c.batches;
+  st->tokens = (int64_t)c.tokens;
+  st->jobs = (int64_t)c.jobs;
+  for (int i = 0; i < 5; ++i) st->phase_cycles[i] = (int64_t)c.phase[i];
 }
 
 // Resets the queue and states after an aborted worklist run.
@@ -1189,6 +1532,8 @@ void reset_worklist_state(dfpr_graph* g) {
   cudaStream_t s = g->stream;
   DFPR_CUDA(cudaMemsetAsync(g->state.p, 0, sizeof(uint32_t) * g->state.count, s));
   k_fill<int32_t><<<grid_small((long long)g->qcap), kNT, 0, s>>>(g->queue.p, (long long)g->qcap, -1);
+  DFPR_LAUNCHED();
+  k_fill<unsigned long long><<<grid_small((long long)g->tcap), kNT, 0, s>>>(g->tokens.p, (long long)g->tcap, ~0ull);
   DFPR_LAUNCHED();
 }
 
@@ -1207,7 +1552,9 @@ dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr
     seeded = g->n;
   }
   const long long work_cap = (long long)p.max_iter * (long long)g->n;
-  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, work_cap, seeded, 1);
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, work_cap, seeded, 1, g->jcap);
+  DFPR_LAUNCHED();
+  k_init_jobs<<<grid_small(g->jcap), kNT, 0, s>>>(g->job_ring.p, g->jcap);
   DFPR_LAUNCHED();
   if (seeded) {
     k_seed_all<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p, g->queue.p);
@@ -1240,7 +1587,7 @@ dfpr_status run_round(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_st
   long long* nsi = nullptr;
   if (kind == kRunDF) nsi = prepare_marking<P>(g, a);
   DFPR_CUDA(cudaEventRecord(e0, s));
-  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 1);
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 1, 0);
   DFPR_LAUNCHED();
   g->pass_ctr.ensure((size_t)p.max_iter + 1, s);
   a.pass_ctr = g->pass_ctr.p;
@@ -1307,9 +1654,9 @@ void swap_vectors<P32>(dfpr_graph* g) {
 }
 
 template <class P>
-void second_vectors(dfpr_graph* g, typename P::val** R2, typename P::val** C2);
+void second_vectors(dfpr_graph* g, typename P::val** R2, typename P::contrib** C2);
 template <>
-void second_vectors<P64>(dfpr_graph* g, double** R2, double** C2) {
+void second_vectors<P64>(dfpr_graph* g, double** R2, long long** C2) {
   if (!g->R64b.p) {
     g->R64b.reset(g->n, g->stream);
     g->C64b.reset(g->n, g->stream);
@@ -1333,21 +1680,23 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
                        cudaEvent_t e0, cudaEvent_t e1) {
   cudaStream_t s = g->stream;
   using V = typename P::val;
-  V *R2 = nullptr, *C2 = nullptr;
+  using CV = typename P::contrib;
+  V* R2 = nullptr;
+  CV* C2 = nullptr;
   second_vectors<P>(g, &R2, &C2);
   Args<P> a = make_args<P>(g, p);
   set_vectors<P>(g, a);
   long long* nsi = nullptr;
   if (kind == kRunDF) nsi = prepare_marking<P>(g, a);
   DFPR_CUDA(cudaEventRecord(e0, s));
-  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 0);
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 0, 0);
   DFPR_LAUNCHED();
   const bool df = kind == kRunDF;
   long long count = g->n;
   if (df) {
     // unaffected vertices keep R_prev in both vectors
     DFPR_CUDA(cudaMemcpyAsync(R2, a.R, sizeof(V) * g->n, cudaMemcpyDeviceToDevice, s));
-    DFPR_CUDA(cudaMemcpyAsync(C2, a.C, sizeof(V) * g->n, cudaMemcpyDeviceToDevice, s));
+    DFPR_CUDA(cudaMemcpyAsync(C2, a.C, sizeof(CV) * g->n, cudaMemcpyDeviceToDevice, s));
     k_mark_list<P><<<grid_small(32ll * g->n), kNT, 0, s>>>(a);
     DFPR_LAUNCHED();
     count = (long long)read_word(g, &g->ctl.p->len.v, sizeof(long long));
@@ -1403,17 +1752,18 @@ void normalize_ranks(dfpr_graph* g) {
   cudaStream_t s = g->stream;
   double* sum = &g->ctl.p->dsum;
   DFPR_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), s));
-  typename P::val *R, *C;
+  typename P::val* R;
+  typename P::contrib* C;
   if constexpr (sizeof(typename P::val) == 8) {
     R = (typename P::val*)g->R64.p;
-    C = (typename P::val*)g->C64.p;
+    C = (typename P::contrib*)g->C64.p;
   } else {
     R = (typename P::val*)g->R32.p;
-    C = (typename P::val*)g->C32.p;
+    C = (typename P::contrib*)g->C32.p;
   }
   k_sum_ranks<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, R, sum);
   DFPR_LAUNCHED();
-  k_scale<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, R, C, sum);
+  k_scale<typename P::val, typename P::contrib><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, R, C, sum);
   DFPR_LAUNCHED();
 }
 
@@ -1479,6 +1829,15 @@ void alloc_iteration_state(dfpr_graph* g) {
   g->queue.reset(q, s);
   k_fill<int32_t><<<grid_small((long long)q), kNT, 0, s>>>(g->queue.p, (long long)q, -1);
   DFPR_LAUNCHED();
+  g->tcap = 1ull << 21;  // chunk tokens in flight at most (slots are reused as they drain)
+  g->tokens.reset(g->tcap, s);
+  k_fill<unsigned long long><<<grid_small((long long)g->tcap), kNT, 0, s>>>(g->tokens.p, (long long)g->tcap, ~0ull);
+  DFPR_LAUNCHED();
+  g->jcap = 4096;  // heavy vertices whose gathers can be split at the same time
+  g->job_ring.reset(g->jcap, s);
+  g->job_v.reset(g->jcap, s);
+  g->job_rem.reset(g->jcap, s);
+  g->job_sum.reset(g->jcap, s);
   g->ctl.reset(1, s);
   DFPR_CUDA(cudaMemsetAsync(g->ctl.p, 0, sizeof(DfCtl), s));
   g->affected_list.reset(n, s);
@@ -1493,9 +1852,9 @@ void alloc_iteration_state(dfpr_graph* g) {
 void reset_ranks(dfpr_graph* g) {
   cudaStream_t s = g->stream;
   if (g->cfg.precision == DFPR_FP64)
-    k_init_ranks<double><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, g->C64.p);
+    k_init_ranks<double, long long><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, g->C64.p);
   else
-    k_init_ranks<float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, g->C32.p);
+    k_init_ranks<float, float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, g->C32.p);
   DFPR_LAUNCHED();
 }
 

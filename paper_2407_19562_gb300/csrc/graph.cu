@@ -313,26 +313,23 @@ __global__ void k_update_rows(const uint32_t* __restrict__ gid_total, long long 
   }
 }
 
-template <typename T>
+template <typename T, typename CT>
 __global__ void k_group_contrib(const uint32_t* __restrict__ gid_total, long long nrc,
                                 const int32_t* __restrict__ gowner,
                                 const long long* __restrict__ newdeg, const T* __restrict__ R,
-                                T* __restrict__ C) {
+                                CT* __restrict__ C) {
   const long long ng = *gid_total;
   GRID_STRIDE(g, nrc) {
     if (g >= ng) continue;
     const int u = gowner[g];
-    C[u] = newdeg[g] > 0 ? R[u] / (T)newdeg[g] : T(0);
+    C[u] = contrib_of(R[u], (int)newdeg[g]);
   }
 }
 
-template <typename T>
+template <typename T, typename CT>
 __global__ void k_contrib_all(int32_t n, const RowDesc* __restrict__ rows, const T* __restrict__ R,
-                              T* __restrict__ C) {
-  GRID_STRIDE(u, n) {
-    const int d = rows[u].deg;
-    C[u] = d > 0 ? R[u] / (T)d : T(0);
-  }
+                              CT* __restrict__ C) {
+  GRID_STRIDE(u, n) C[u] = contrib_of(R[u], rows[u].deg);
 }
 
 // Appends the groups' sources and the deletion targets to the pending change
@@ -590,9 +587,9 @@ void apply_direction(dfpr_graph* g, Rows& dir, const unsigned long long* rc, lon
   if (!csr) return;
   // contributions of the changed sources use their new out-degree
   if (g->cfg.precision == DFPR_FP64)
-    k_group_contrib<double><<<gr, NT, 0, s>>>(gid + nrc, nrc, gowner, newdeg, g->R64.p, g->C64.p);
+    k_group_contrib<double, long long><<<gr, NT, 0, s>>>(gid + nrc, nrc, gowner, newdeg, g->R64.p, g->C64.p);
   else
-    k_group_contrib<float><<<gr, NT, 0, s>>>(gid + nrc, nrc, gowner, newdeg, g->R32.p, g->C32.p);
+    k_group_contrib<float, float><<<gr, NT, 0, s>>>(gid + nrc, nrc, gowner, newdeg, g->R32.p, g->C32.p);
   DFPR_LAUNCHED();
   // pending change set: sources (marking of out-rows) and deletion targets
   const long long nd = g->last_real_del;
@@ -729,9 +726,9 @@ void graph_export(dfpr_graph* g, const Rows& dir, long long* offsets, int32_t* i
 void refresh_contributions(dfpr_graph* g) {
   cudaStream_t s = g->stream;
   if (g->cfg.precision == DFPR_FP64)
-    k_contrib_all<double><<<grid_for(g->n), NT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, g->C64.p);
+    k_contrib_all<double, long long><<<grid_for(g->n), NT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, g->C64.p);
   else
-    k_contrib_all<float><<<grid_for(g->n), NT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, g->C32.p);
+    k_contrib_all<float, float><<<grid_for(g->n), NT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, g->C32.p);
   DFPR_LAUNCHED();
 }
 
