@@ -82,7 +82,9 @@ typedef struct dfpr_graph_config {
   double row_slack;   /* extra capacity per row as a fraction of its degree, so
                          batches update rows in place (default 0.125) */
   int32_t min_slack;  /* minimum extra capacity per row (default 2) */
-  int32_t reserved;
+  int32_t reorder;    /* 1 (default): number vertices internally by decreasing degree,
+                         so that frequently read ranks share memory sectors; ids at the
+                         interface stay the caller's. 0: keep the caller's numbering */
   double tail_slack;  /* spare edge capacity for rows that outgrow their slot,
                          as a fraction of the edge count (default 0.125) */
 } dfpr_graph_config;

@@ -48,7 +48,7 @@ class DfprError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("dead_end", ctypes.c_int32),
                 ("row_slack", ctypes.c_double), ("min_slack", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tail_slack", ctypes.c_double)]
+                ("reorder", ctypes.c_int32), ("tail_slack", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):

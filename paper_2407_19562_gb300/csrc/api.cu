@@ -70,11 +70,17 @@ constexpr int kNT = 256;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
        i += (long long)gridDim.x * blockDim.x)
 
-__global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, long long n) {
-  GRID_STRIDE(i, n) out[i] = (double)in[i];
+// out[u] = in[perm[u]] (caller order from internal order; perm may be null).
+template <class T>
+__global__ void k_ranks_out(const T* __restrict__ in, const int32_t* __restrict__ perm,
+                            double* __restrict__ out, long long n) {
+  GRID_STRIDE(u, n) out[u] = (double)in[perm ? perm[u] : u];
 }
-__global__ void k_narrow(const double* __restrict__ in, float* __restrict__ out, long long n) {
-  GRID_STRIDE(i, n) out[i] = (float)in[i];
+// out[perm[u]] = in[u] (internal order from caller order).
+template <class T>
+__global__ void k_ranks_in(const double* __restrict__ in, const int32_t* __restrict__ perm,
+                           T* __restrict__ out, long long n) {
+  GRID_STRIDE(u, n) out[perm ? perm[u] : u] = (T)in[u];
 }
 
 // Makes the graph's device current for the duration of a call.
@@ -180,6 +186,7 @@ void dfpr_default_config(dfpr_graph_config* cfg) {
   cfg->dead_end = DFPR_SELF_LOOPS;
   cfg->row_slack = 0.125;
   cfg->min_slack = 2;
+  cfg->reorder = 1;
   cfg->tail_slack = 0.125;
 }
 
@@ -407,7 +414,8 @@ dfpr_status dfpr_get_ranks(const dfpr_graph* gc, double* out, int on_device) {
   DeviceGuard dg(g->device);
   cudaStream_t s = g->stream;
   const long long n = g->n;
-  if (g->cfg.precision == DFPR_FP64) {
+  const int32_t* perm = g->relabeled ? g->perm.p : nullptr;
+  if (g->cfg.precision == DFPR_FP64 && !perm) {
     DFPR_CUDA(cudaMemcpyAsync(out, g->R64.p, sizeof(double) * n,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   } else {
@@ -417,7 +425,10 @@ dfpr_status dfpr_get_ranks(const dfpr_graph* gc, double* out, int on_device) {
       tmp.reset((size_t)n, s);
       dst = tmp.p;
     }
-    k_widen<<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(g->R32.p, dst, n);
+    if (g->cfg.precision == DFPR_FP64)
+      k_ranks_out<double><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(g->R64.p, perm, dst, n);
+    else
+      k_ranks_out<float><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(g->R32.p, perm, dst, n);
     DFPR_LAUNCHED();
     if (!on_device)
       DFPR_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -438,13 +449,17 @@ dfpr_status dfpr_set_ranks(dfpr_graph* g, const double* ranks, int on_device) {
   DeviceGuard dg(g->device);
   cudaStream_t s = g->stream;
   const long long n = g->n;
-  if (g->cfg.precision == DFPR_FP64) {
+  const int32_t* perm = g->relabeled ? g->perm.p : nullptr;
+  if (g->cfg.precision == DFPR_FP64 && !perm) {
     DFPR_CUDA(cudaMemcpyAsync(g->R64.p, ranks, sizeof(double) * n,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   } else {
     DevArray<double> tmp;
     const double* srcp = stage_in(g, tmp, ranks, n, on_device);
-    k_narrow<<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(srcp, g->R32.p, n);
+    if (g->cfg.precision == DFPR_FP64)
+      k_ranks_in<double><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(srcp, perm, g->R64.p, n);
+    else
+      k_ranks_in<float><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(srcp, perm, g->R32.p, n);
     DFPR_LAUNCHED();
   }
   refresh_contributions(g);

@@ -221,6 +221,9 @@ struct dfpr_graph {
   dfpr::DevArray<uint32_t> rc_bits;       // round mode: not-converged bitmap
   dfpr::DevArray<unsigned long long> pass_ctr;  // round mode: per-pass claim counters
   dfpr::DevArray<uint32_t> item_done;     // round mode: marking items completed (helping)
+  dfpr::DevArray<int32_t> perm;           // caller id -> internal id (when reordered)
+  dfpr::DevArray<int32_t> iperm;          // internal id -> caller id
+  bool relabeled = false;
   dfpr::Pending pend;
   dfpr::Scratch scratch;
   dfpr::DevArray<unsigned long long> host_sync;  // small device words read back

@@ -27,6 +27,7 @@
 // the kernel records DFPR_ETIMEOUT and returns.
 #include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <vector>
 
 #include "df.cuh"
@@ -143,6 +144,17 @@ struct P32 {
 // ---------------------------------------------------------------------------
 // Kernel arguments
 // ---------------------------------------------------------------------------
+
+// Frontier threshold of a vertex with new rank r: tau_f absolute (FP64), or
+// tau_f relative to r but at least one unit in the last place of r (FP32: a
+// threshold below one ulp would expand on every rounding jitter).
+template <class P>
+__device__ __forceinline__ double frontier_thr(double tol_f, typename P::val r) {
+  if (!P::relative) return tol_f;
+  const float fr = fabsf((float)r);
+  const float ulp = __int_as_float(__float_as_int(fr) & 0x7f800000) * 1.1920928955078125e-7f;
+  return fmax(tol_f * (double)fr, (double)ulp);
+}
 
 template <class P>
 struct Args {
@@ -649,7 +661,7 @@ __device__ __forceinline__ void vertex_epilogue(const Args<P>& a, int v, double 
   const double dr = fabs((double)r - (double)r_old);
   a.R[v] = r;
   a.C[v] = contrib_of(r, od);
-  const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
+  const double thr_f = frontier_thr<P>(a.tol_f, r);
   const double thr = P::relative ? a.tol * fabs((double)r) : a.tol;
   expand = fabs((double)r - (double)x0) > thr_f;
   a.X[v] = expand ? r : x0;
@@ -1092,7 +1104,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         const int od = a.out_rows[v].deg;
         a.R[v] = r;
         a.C[v] = contrib_of(r, od);
-        const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
+        const double thr_f = frontier_thr<P>(a.tol_f, r);
         thr = P::relative ? a.tol * fabs((double)r) : a.tol;
         expand = dr > thr_f;
         st.max_change = fmax(st.max_change, dr);
@@ -1201,7 +1213,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
       const int od = a.out_rows[v].deg;
       Rout[v] = r;
       Cout[v] = contrib_of(r, od);
-      const double thr_f = P::relative ? a.tol_f * fabs((double)r) : a.tol_f;
+      const double thr_f = frontier_thr<P>(a.tol_f, r);
       expand = frontier && dr > thr_f;
       st.max_change = fmax(st.max_change, dr);
       if (expand) st.expansions++;
@@ -1341,8 +1353,13 @@ __global__ void k_init_ranks(int32_t n, const RowDesc* __restrict__ out_rows, T*
   }
 }
 
-__global__ void k_export_state(int32_t n, const uint32_t* __restrict__ state, uint8_t* out) {
-  GRID_STRIDE(v, n) out[v] = ((state[v >> 4] >> ((v & 15) * 2)) & 3u) ? 1 : 0;
+// Flags in caller order: out[u] for internal vertex perm[u] (perm may be null).
+__global__ void k_export_state(int32_t n, const uint32_t* __restrict__ state,
+                               const int32_t* __restrict__ perm, uint8_t* out) {
+  GRID_STRIDE(u, n) {
+    const int v = perm ? perm[u] : (int)u;
+    out[u] = ((state[v >> 4] >> ((v & 15) * 2)) & 3u) ? 1 : 0;
+  }
 }
 
 
@@ -1402,9 +1419,11 @@ __global__ void k_scale(int32_t n, const RowDesc* __restrict__ out_rows, T* R, C
   }
 }
 
-// ND / static round schedule: the affected list is every vertex.
-__global__ void k_seed_round(int32_t n, int32_t* alist, DfCtl* c) {
-  GRID_STRIDE(i, n) alist[i] = (int32_t)i;
+// ND / static round schedule: the affected list is every vertex, visited with
+// a stride coprime to n so that the densest vertices (low internal ids) are
+// spread over the pass instead of filling its first chunks.
+__global__ void k_seed_round(int32_t n, long long stride, int32_t* alist, DfCtl* c) {
+  GRID_STRIDE(i, n) alist[i] = (int32_t)(((long long)i * stride) % n);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->len.v = n;
     c->nc.v = n;
@@ -1603,7 +1622,10 @@ dfpr_status run_round(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_st
     // ND / static: every vertex is affected and not converged from the start
     DFPR_CUDA(cudaMemsetAsync(g->va_bits.p, 0xff, sizeof(uint32_t) * g->va_bits.count, s));
     DFPR_CUDA(cudaMemsetAsync(g->rc_bits.p, 0xff, sizeof(uint32_t) * g->rc_bits.count, s));
-    k_seed_round<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->affected_list.p, g->ctl.p);
+    long long stride = ((long long)((double)g->n * 0.6180339887498949)) | 1;
+    while (std::gcd(stride, (long long)g->n) != 1) stride += 2;
+    k_seed_round<<<grid_small(g->n), kNT, 0, s>>>(g->n, stride % g->n == 0 ? 1 : stride,
+                                                  g->affected_list.p, g->ctl.p);
     DFPR_LAUNCHED();
   }
   // One CTA per 1024 vertices at most: with many more warps than 32-vertex
@@ -1891,7 +1913,8 @@ void initial_affected(dfpr_graph* g, uint8_t* affected_dev, long long* count) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   DFPR_REQUIRE(r == DFPR_OK, r, "dfpr_initial_affected: marking did not complete");
-  k_export_state<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p, affected_dev);
+  k_export_state<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p,
+                                                  g->relabeled ? g->perm.p : nullptr, affected_dev);
   DFPR_LAUNCHED();
   CtlHost h = read_ctl(g);
   if (count) *count = (long long)h.c.tail.v;

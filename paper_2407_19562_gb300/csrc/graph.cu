@@ -139,7 +139,8 @@ __global__ void k_transpose2(const unsigned long long* __restrict__ k, long long
 // Batch keys: (owner << (bits + 1)) | (other << 1) | type, type 0 = deletion.
 __global__ void k_batch_keys(const int32_t* ds, const int32_t* dd, long long nd, const int32_t* is,
                              const int32_t* id, long long ni, int32_t n, int bits,
-                             unsigned long long* keys, unsigned long long* err) {
+                             const int32_t* __restrict__ perm, unsigned long long* keys,
+                             unsigned long long* err) {
   GRID_STRIDE(i, nd + ni) {
     const bool del = i < nd;
     int a = del ? ds[i] : is[i - nd];
@@ -148,6 +149,10 @@ __global__ void k_batch_keys(const int32_t* ds, const int32_t* dd, long long nd,
       atomicOr(err, 1ull);
       a = 0;
       b = 0;
+    }
+    if (perm) {  // caller ids -> internal ids
+      a = perm[a];
+      b = perm[b];
     }
     keys[i] = ((unsigned long long)a << (bits + 1)) | ((unsigned long long)b << 1) | (del ? 0ull : 1ull);
   }
@@ -401,6 +406,71 @@ __global__ void k_not_in(const unsigned long long* __restrict__ keys, long long 
   }
 }
 
+__global__ void k_degree_count(const unsigned long long* __restrict__ k, long long m, int bits,
+                               uint32_t* deg) {
+  const unsigned long long mask = (1ull << bits) - 1;
+  GRID_STRIDE(i, m) {
+    atomicAdd(deg + (k[i] >> bits), 1u);
+    atomicAdd(deg + (k[i] & mask), 1u);
+  }
+}
+
+// Sort key of a vertex: decreasing degree, then increasing id.
+__global__ void k_vertex_keys(const uint32_t* __restrict__ deg, int32_t n, unsigned long long* key) {
+  GRID_STRIDE(u, n) key[u] = ((unsigned long long)(0xffffffffu - deg[u]) << 32) | (unsigned)u;
+}
+
+__global__ void k_perm_from_sorted(const unsigned long long* __restrict__ sorted, int32_t n,
+                                   int32_t* perm, int32_t* iperm) {
+  GRID_STRIDE(i, n) {
+    const int32_t u = (int32_t)(sorted[i] & 0xffffffffull);
+    iperm[i] = u;
+    perm[u] = (int32_t)i;
+  }
+}
+
+__global__ void k_relabel_keys(unsigned long long* k, long long m, int bits,
+                               const int32_t* __restrict__ perm) {
+  const unsigned long long mask = (1ull << bits) - 1;
+  GRID_STRIDE(i, m) {
+    const unsigned a = (unsigned)perm[k[i] >> bits], b = (unsigned)perm[k[i] & mask];
+    k[i] = pack2(a, b, bits);
+  }
+}
+
+// Packed keys (caller_row << bits | caller_col) of every edge of one direction.
+__global__ void k_export_keys(const RowDesc* __restrict__ rows, const int32_t* __restrict__ edges,
+                              int32_t n, const long long* __restrict__ poff,
+                              const int32_t* __restrict__ iperm, int bits,
+                              unsigned long long* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = warp; i < n; i += nwarps) {
+    const RowDesc r = rows[i];
+    const long long o = poff[i];
+    const unsigned ru = (unsigned)iperm[i];
+    for (int e = lane; e < r.deg; e += 32) keys[o + e] = pack2(ru, (unsigned)iperm[edges[r.off + e]], bits);
+  }
+}
+
+__global__ void k_keys_to_csr(const unsigned long long* __restrict__ k, long long m, int bits,
+                              int32_t* idx, long long* first, long long* last) {
+  const unsigned long long mask = (1ull << bits) - 1;
+  GRID_STRIDE(i, m) {
+    const unsigned a = (unsigned)(k[i] >> bits);
+    idx[i] = (int32_t)(k[i] & mask);
+    if (i == 0 || (unsigned)(k[i - 1] >> bits) != a) first[a] = i;
+    if (i == m - 1 || (unsigned)(k[i + 1] >> bits) != a) last[a] = i + 1;
+  }
+}
+
+__global__ void k_offsets_from_bounds(const long long* __restrict__ first,
+                                      const long long* __restrict__ last, int32_t n,
+                                      long long* deg) {
+  GRID_STRIDE(u, n) deg[u] = last[u] - first[u];
+}
+
 unsigned grid_for(long long n) { return blocks_for(n, NT, 152u * 32u); }
 
 }  // namespace
@@ -647,6 +717,34 @@ void graph_build(dfpr_graph* g, const int32_t* src, const int32_t* dst, long lon
     DFPR_LAUNCHED();
     m = (long long)(uint32_t)read_word(g, pos.p + nk, sizeof(uint32_t));
   }
+  if (g->cfg.reorder && n > 1) {
+    // Internal numbering by decreasing total degree (ties by caller id): the
+    // most frequently read ranks, contributions and flags then share sectors.
+    DevArray<uint32_t> deg;
+    DevArray<unsigned long long> vk, vt;
+    deg.reset(n, s);
+    vk.reset(n, s);
+    vt.reset(n, s);
+    DFPR_CUDA(cudaMemsetAsync(deg.p, 0, sizeof(uint32_t) * n, s));
+    if (m > 0) {
+      k_degree_count<<<grid_for(m), NT, 0, s>>>(other, m, g->bits, deg.p);
+      DFPR_LAUNCHED();
+    }
+    k_vertex_keys<<<grid_for(n), NT, 0, s>>>(deg.p, n, vk.p);
+    DFPR_LAUNCHED();
+    unsigned long long* vs = radix_sort_u64(vk.p, vt.p, n, 64, sc, s);
+    g->perm.reset(n, s);
+    g->iperm.reset(n, s);
+    k_perm_from_sorted<<<grid_for(n), NT, 0, s>>>(vs, n, g->perm.p, g->iperm.p);
+    DFPR_LAUNCHED();
+    g->relabeled = true;
+    if (m > 0) {
+      k_relabel_keys<<<grid_for(m), NT, 0, s>>>(other, m, g->bits, g->perm.p);
+      DFPR_LAUNCHED();
+      unsigned long long* rs = radix_sort_u64(other, sorted, m, 2 * g->bits, sc, s);
+      if (rs != other) std::swap(sorted, other);
+    }
+  }
   build_direction(g, g->out, other, m);
   // CSC: transposed keys, sorted
   k_transpose2<<<grid_for(m), NT, 0, s>>>(other, m, g->bits, sorted);
@@ -671,7 +769,8 @@ void graph_apply(dfpr_graph* g, const int32_t* ds, const int32_t* dd, long long 
   uint32_t* flag = sc.get<uint32_t>(kSBFlag, (size_t)nb + 1, s);
   uint32_t* pos = sc.get<uint32_t>(kSBPos, (size_t)nb + 1, s);
   DFPR_CUDA(cudaMemsetAsync(words, 0, sizeof(unsigned long long) * 3, s));
-  k_batch_keys<<<grid_for(nb), NT, 0, s>>>(ds, dd, nd, is, id, ni, g->n, bits, keys, words + kWErr);
+  k_batch_keys<<<grid_for(nb), NT, 0, s>>>(ds, dd, nd, is, id, ni, g->n, bits,
+                                           g->relabeled ? g->perm.p : nullptr, keys, words + kWErr);
   DFPR_LAUNCHED();
   if (read_word(g, words + kWErr, 8) != 0) {
     set_error("dfpr_apply_batch: a vertex id is outside [0, n)");
@@ -714,6 +813,34 @@ void graph_apply(dfpr_graph* g, const int32_t* ds, const int32_t* dd, long long 
 void graph_export(dfpr_graph* g, const Rows& dir, long long* offsets, int32_t* idx) {
   cudaStream_t s = g->stream;
   const int32_t n = g->n;
+  if (g->relabeled) {
+    // caller ids: every edge as a (caller row, caller column) key, sorted
+    long long* deg = g->scratch.get<long long>(kSCap, n, s);
+    long long* poff = g->scratch.get<long long>(kSOff, (size_t)n + 1, s);
+    k_deg_of<<<grid_for(n), NT, 0, s>>>(dir.rows.p, n, deg);
+    DFPR_LAUNCHED();
+    scan_exclusive_i64(deg, poff, n, poff + n, g->scratch, s);
+    const long long m = g->m;
+    DevArray<unsigned long long> keys, tmp;
+    keys.reset((size_t)m + 1, s);
+    tmp.reset((size_t)m + 1, s);
+    k_export_keys<<<grid_for(32ll * n), NT, 0, s>>>(dir.rows.p, dir.edges.p, n, poff, g->iperm.p,
+                                                     g->bits, keys.p);
+    DFPR_LAUNCHED();
+    unsigned long long* sk = radix_sort_u64(keys.p, tmp.p, m, 2 * g->bits, g->scratch, s);
+    long long* first = g->scratch.get<long long>(kSFirst, n, s);
+    long long* last = g->scratch.get<long long>(kSLast, n, s);
+    DFPR_CUDA(cudaMemsetAsync(first, 0, sizeof(long long) * n, s));
+    DFPR_CUDA(cudaMemsetAsync(last, 0, sizeof(long long) * n, s));
+    if (m > 0) {
+      k_keys_to_csr<<<grid_for(m), NT, 0, s>>>(sk, m, g->bits, idx, first, last);
+      DFPR_LAUNCHED();
+    }
+    k_offsets_from_bounds<<<grid_for(n), NT, 0, s>>>(first, last, n, deg);
+    DFPR_LAUNCHED();
+    scan_exclusive_i64(deg, offsets, n, offsets + n, g->scratch, s);
+    return;
+  }
   long long* deg = g->scratch.get<long long>(kSCap, n, s);
   k_deg_of<<<grid_for(n), NT, 0, s>>>(dir.rows.p, n, deg);
   DFPR_LAUNCHED();

@@ -381,3 +381,21 @@ def test_grid_local_batch(gpu_lib):
     assert st.status == gpu_lib.OK
     assert np.max(np.abs(g.get_ranks() - ref1)) <= LINF64
     assert st.affected < n // 2  # a localised batch touches a small region
+
+
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_caller_numbering_kept_with_and_without_reorder(gpu_lib, c1, reorder):
+    """The internal degree ordering is invisible at the interface: graph exports,
+    ranks and the initial frontier come back in the caller's ids either way."""
+    cfg = gpu_lib.default_config(reorder=reorder)
+    g = gpu_lib.graph_load(c1["n"], c1["src"], c1["dst"], cfg)
+    check_graph(g, c1["g0"])
+    g.set_ranks(c1["R0ref"])
+    assert np.array_equal(g.get_ranks(), c1["R0ref"])
+    assert g.apply_batch(*c1["batch"]) == c1["nreal"]
+    check_graph(g, c1["g1"])
+    flags, _ = g.initial_affected()
+    assert np.array_equal(flags, c1["g1"].initial_affected())
+    st = g.df_pagerank()
+    assert st.status == gpu_lib.OK
+    assert np.max(np.abs(g.get_ranks() - c1["ref1"])) <= LINF64
