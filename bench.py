@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat14", "grid4096"], default="rmat24")
+    ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat14", "grid4096", "many256"],
+                    default="rmat24")
+    ap.add_argument("--graphs", type=int, default=256, help="many256: number of graphs")
     ap.add_argument("--batch-frac", type=float, default=1e-4)
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--mode", choices=["worklist", "round", "jacobi"], default="worklist")
@@ -362,10 +364,116 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs, np.float64), q)) if len(xs) else None
+
+
+def run_many(args):
+    """Many graphs in one persistent launch per step (a set loaded with
+    dfpr_graph_load_parts) against plain per-graph DF, one graph after another,
+    on the same GPU. Per-graph latency of a step: from the step's start to the
+    end of that graph's last recomputation."""
+    import torch
+
+    import paper_2407_19562_gb300 as dfpr
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    specs = workloads.many_graph_specs(args.graphs, 1000)
+    graphs, off = [], [0]
+    for i, (n, deg, frac) in enumerate(specs):
+        n, src, dst = workloads.rmat_graph_n(n, deg, 1000 + i)
+        graphs.append((n, src, dst, frac))
+        off.append(off[-1] + n)
+    off = np.array(off, np.int64)
+    gsrc = np.concatenate([g[1] + o for g, o in zip(graphs, off)]).astype(np.int32)
+    gdst = np.concatenate([g[2] + o for g, o in zip(graphs, off)]).astype(np.int32)
+    prec = dfpr.FP64 if args.precision == "fp64" else dfpr.FP32
+    tol = 1e-10 if args.precision == "fp64" else 1e-7
+    cfg = dfpr.default_config(precision=prec)
+    s_set = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=stream.cuda_stream)
+    st0 = dfpr.static_pagerank(s_set, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
+    R0 = dfpr.get_ranks(s_set)
+    singles = []
+    for i, (n, src, dst, frac) in enumerate(graphs):
+        g = dfpr.graph_load(n, src, dst, cfg, stream=stream.cuda_stream)
+        dfpr.set_ranks(g, np.ascontiguousarray(R0[off[i]:off[i + 1]]))
+        singles.append(g)
+    params = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
+    total = args.warmup + args.steps
+
+    def batches_for(step):
+        out = []
+        for i, (n, src, dst, frac) in enumerate(graphs):
+            b = max(1, int(round(frac * len(src))))
+            out.append(workloads.uniform_batch(n, b, 7000 + 1000 * step + i, src, dst))
+        return out
+
+    set_lat, single_lat, set_step, single_step, set_kernel = [], [], [], [], []
+    for step in range(total):
+        bl = batches_for(step)
+        gb = [np.concatenate([b[k] + o for b, o in zip(bl, off)]).astype(np.int32) for k in range(4)]
+        dev_gb = [torch.from_numpy(x).cuda() for x in gb]
+        dev_bl = [[torch.from_numpy(x).cuda() for x in b] for b in bl]
+        torch.cuda.synchronize()
+        # the set: one apply + one persistent launch for every graph
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dfpr.apply_batch(s_set, *dev_gb)
+        st = dfpr.df_pagerank(s_set, params)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1)
+        part = dfpr.get_part_times(s_set)
+        overhead = step_ms - st.ms
+        lat = [overhead + t for t in part]
+        # plain per-batch DF: each graph alone, one after another
+        t_acc, lat1 = 0.0, []
+        s0 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        evs = []
+        for i, g in enumerate(singles):
+            dfpr.apply_batch(g, *dev_bl[i])
+            dfpr.df_pagerank(g, params)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            evs.append(ev)
+        torch.cuda.synchronize()
+        lat1 = [s0.elapsed_time(ev) for ev in evs]
+        if step >= args.warmup:
+            set_lat += lat
+            single_lat += lat1
+            set_step.append(step_ms)
+            single_step.append(lat1[-1])
+            set_kernel.append(st.ms)
+    # both forms reach the same ranks (each graph's update is the same method)
+    Rs = dfpr.get_ranks(s_set)
+    diff = max(float(np.max(np.abs(Rs[off[i]:off[i + 1]] - dfpr.get_ranks(g))))
+               for i, g in enumerate(singles))
+    line = {
+        "metric": "many-graph DF: ms/step and per-graph p50/p99 latency (batched vs per-graph)",
+        "value": float(np.mean(set_step)), "unit": "ms/step", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "dtype": "f64" if prec == dfpr.FP64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"many{args.graphs}: R-MAT n log-uniform [1e3,1e6], avg degree U[4,32], "
+                               "batches 0.1-1% of each graph's edges (80/20)",
+                   "graphs": args.graphs, "n_total": int(off[-1]), "m_raw_total": int(len(gsrc)),
+                   "precision": args.precision},
+        "batched": {"ms_per_step": float(np.mean(set_step)), "kernel_ms": float(np.mean(set_kernel)),
+                    "p50_ms": pct(set_lat, 50), "p99_ms": pct(set_lat, 99)},
+        "per_graph_sequential": {"ms_per_step": float(np.mean(single_step)),
+                                 "p50_ms": pct(single_lat, 50), "p99_ms": pct(single_lat, 99)},
+        "max_abs_diff_batched_vs_alone": diff,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "many256":
+        run_many(args)
     else:
         run_ours(args)
 

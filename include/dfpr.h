@@ -144,6 +144,33 @@ dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int3
                             int on_device, void* cuda_stream, const dfpr_graph_config* cfg,
                             dfpr_graph** out);
 
+/*
+ * Loads k independent graphs as one device-resident set (a disjoint union):
+ * graph i owns the global vertex ids [vertex_offsets[i], vertex_offsets[i+1])
+ * (host array of k + 1 entries, vertex_offsets[0] = 0, nondecreasing, each
+ * graph non-empty), and src/dst (host or device, m entries) use global ids.
+ * An edge joining two graphs is an error (EINVAL). Eq. 1 (Sec. 3.1) is
+ * applied per graph: the teleport term of a vertex is (1 - alpha) / n_i of
+ * its own graph, and static ranks start at 1 / n_i. Every later call works on
+ * all graphs at once: one dfpr_apply_batch takes the batches of every graph
+ * (global ids) and one dfpr_df_pagerank runs all their frontiers in a single
+ * persistent launch. Not supported with DFPR_TELEPORT or normalize = 1.
+ */
+dfpr_status dfpr_graph_load_parts(int32_t k, const int32_t* vertex_offsets, int64_t m,
+                                  const int32_t* src, const int32_t* dst, int on_device,
+                                  void* cuda_stream, const dfpr_graph_config* cfg,
+                                  dfpr_graph** out);
+
+/* Number of graphs in the set (1 for dfpr_graph_load). */
+dfpr_status dfpr_graph_parts(const dfpr_graph* g, int32_t* k);
+
+/*
+ * Per-graph completion times of the last worklist update, in ms after its
+ * persistent kernel started (host array of k doubles): the time the last
+ * recomputation of a vertex of graph i ended, 0 when graph i had no work.
+ */
+dfpr_status dfpr_get_part_times(const dfpr_graph* g, double* ms);
+
 /* Releases every device and host resource of g (NULL is a no-op). */
 dfpr_status dfpr_graph_free(dfpr_graph* g);
 

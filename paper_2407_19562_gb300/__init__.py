@@ -27,6 +27,7 @@ __all__ = [
     "default_config", "default_params", "graph_load", "graph_free", "graph_info",
     "graph_set_stream", "apply_batch", "df_pagerank", "nd_pagerank", "static_pagerank",
     "get_ranks", "set_ranks", "get_csr", "get_csc", "initial_affected", "set_allocator",
+    "graph_load_parts", "get_part_times",
     "use_torch_allocator", "OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "EBUSY",
     "FP64", "FP32", "SELF_LOOPS", "TELEPORT", "WORKLIST", "ROUND", "JACOBI",
 ]
@@ -100,6 +101,10 @@ def load():
             "dfpr_default_params": (None, [ctypes.POINTER(Params)]),
             "dfpr_graph_load": (st, [i32, i64, vp, vp, ci, vp, ctypes.POINTER(Config),
                                      ctypes.POINTER(vp)]),
+            "dfpr_graph_load_parts": (st, [i32, vp, i64, vp, vp, ci, vp, ctypes.POINTER(Config),
+                                           ctypes.POINTER(vp)]),
+            "dfpr_graph_parts": (st, [vp, ctypes.POINTER(i32)]),
+            "dfpr_get_part_times": (st, [vp, vp]),
             "dfpr_graph_free": (st, [vp]),
             "dfpr_graph_set_stream": (st, [vp, vp]),
             "dfpr_graph_info": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -287,6 +292,36 @@ def graph_load(n: int, src, dst, config: Config | None = None, stream="torch") -
                                ctypes.byref(config) if config is not None else None,
                                ctypes.byref(h)), "graph_load")
     return Graph(h.value, int(n))
+
+
+def graph_load_parts(vertex_offsets, src, dst, config: Config | None = None,
+                     stream="torch") -> Graph:
+    """dfpr_graph_load_parts: k graphs as one set; vertex_offsets has k + 1
+    entries and src/dst use global ids."""
+    lib = load()
+    off = np.ascontiguousarray(vertex_offsets, dtype=np.int32)
+    ps, ms, ds = _ptr(src, np.int32, name="src")
+    pd, md, dd = _ptr(dst, np.int32, name="dst")
+    if ms != md:
+        raise DfprError(EINVAL, "graph_load_parts", "src and dst lengths differ")
+    on_dev = _side(ds, dd)
+    s = _torch_stream() if stream == "torch" else stream
+    h = ctypes.c_void_p()
+    _check(lib.dfpr_graph_load_parts(len(off) - 1, off.ctypes.data, ms, ps, pd, on_dev, s,
+                                     ctypes.byref(config) if config is not None else None,
+                                     ctypes.byref(h)), "graph_load_parts")
+    g = Graph(h.value, int(off[-1]))
+    g.parts = len(off) - 1
+    return g
+
+
+def get_part_times(g: Graph) -> np.ndarray:
+    """dfpr_get_part_times: per-graph completion ms of the last worklist update."""
+    k = ctypes.c_int32()
+    _check(load().dfpr_graph_parts(g.handle, ctypes.byref(k)), "graph_parts")
+    out = np.zeros(k.value, np.float64)
+    _check(load().dfpr_get_part_times(g.handle, out.ctypes.data), "get_part_times")
+    return out
 
 
 def graph_free(g: Graph):

@@ -137,6 +137,8 @@ dfpr_status run_call(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, RunKi
   if (pp) p = *pp;
   else dfpr_default_params(&p);
   check_params(p);
+  DFPR_REQUIRE(!(p.normalize && g->nparts > 1), DFPR_EINVAL,
+               "normalize is not supported for a set of graphs");
   if (g->cfg.dead_end == DFPR_TELEPORT)
     DFPR_REQUIRE(kind != kRunDF && p.mode == DFPR_MODE_JACOBI, DFPR_EINVAL,
                  "teleport dead-end handling is supported by the jacobi static / naive-dynamic "
@@ -221,9 +223,9 @@ dfpr_status dfpr_set_allocator(dfpr_alloc_fn alloc, dfpr_free_fn free_fn, void* 
   return DFPR_OK;
 }
 
-dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                            int on_device, void* cuda_stream, const dfpr_graph_config* cfg,
-                            dfpr_graph** out) {
+static dfpr_status load_impl(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                             int on_device, void* cuda_stream, const dfpr_graph_config* cfg,
+                             int32_t k, const int32_t* vertex_offsets, dfpr_graph** out) {
   set_error("");
   if (!out) {
     set_error("dfpr_graph_load: out is NULL");
@@ -243,6 +245,10 @@ dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int3
     set_error("dfpr_graph_load: invalid config");
     return DFPR_EINVAL;
   }
+  if (k > 1 && c.dead_end == DFPR_TELEPORT) {
+    set_error("dfpr_graph_load_parts: teleport dead-end handling is not supported for a set");
+    return DFPR_EINVAL;
+  }
   dfpr_graph* g = nullptr;
   API_BEGIN
   g = new dfpr_graph();
@@ -260,6 +266,16 @@ dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int3
   DFPR_CUDA(cudaMallocHost(&g->pinned, 16 * sizeof(unsigned long long)));
   g->host_sync.reset(16, g->stream);
   DFPR_CUDA(cudaMemsetAsync(g->host_sync.p, 0, 16 * sizeof(unsigned long long), g->stream));
+  if (k > 1) {
+    g->nparts = k;
+    g->part_off_host.assign(vertex_offsets, vertex_offsets + k + 1);
+    g->part_off.reset((size_t)k + 1, g->stream);
+    DFPR_CUDA(cudaMemcpyAsync(g->part_off.p, g->part_off_host.data(), sizeof(int32_t) * (k + 1),
+                              cudaMemcpyHostToDevice, g->stream));
+    g->part_done.reset((size_t)k, g->stream);
+    DFPR_CUDA(cudaMemsetAsync(g->part_done.p, 0, sizeof(unsigned long long) * k, g->stream));
+    g->part_ms.assign((size_t)k, 0.0);
+  }
   {
     DevArray<int32_t> ts, td;
     const int32_t* ds = stage_in(g, ts, src, m, on_device);
@@ -287,6 +303,47 @@ dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int3
     set_error("unexpected internal error");
     return DFPR_ECUDA;
   }
+}
+
+dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                            int on_device, void* cuda_stream, const dfpr_graph_config* cfg,
+                            dfpr_graph** out) {
+  return load_impl(n, m, src, dst, on_device, cuda_stream, cfg, 1, nullptr, out);
+}
+
+dfpr_status dfpr_graph_load_parts(int32_t k, const int32_t* vertex_offsets, int64_t m,
+                                  const int32_t* src, const int32_t* dst, int on_device,
+                                  void* cuda_stream, const dfpr_graph_config* cfg,
+                                  dfpr_graph** out) {
+  if (out) *out = nullptr;
+  if (k < 1 || !vertex_offsets || vertex_offsets[0] != 0) {
+    set_error("dfpr_graph_load_parts: need k >= 1 and vertex_offsets[0] == 0");
+    return DFPR_EINVAL;
+  }
+  for (int32_t i = 0; i < k; ++i)
+    if (vertex_offsets[i + 1] <= vertex_offsets[i]) {
+      set_error("dfpr_graph_load_parts: every graph needs at least one vertex (offsets must increase)");
+      return DFPR_EINVAL;
+    }
+  return load_impl(vertex_offsets[k], m, src, dst, on_device, cuda_stream, cfg, k, vertex_offsets, out);
+}
+
+dfpr_status dfpr_graph_parts(const dfpr_graph* g, int32_t* k) {
+  if (!g || !k) {
+    set_error("dfpr_graph_parts: NULL argument");
+    return DFPR_EINVAL;
+  }
+  *k = g->nparts;
+  return DFPR_OK;
+}
+
+dfpr_status dfpr_get_part_times(const dfpr_graph* g, double* ms) {
+  if (!g || !ms) {
+    set_error("dfpr_get_part_times: NULL argument");
+    return DFPR_EINVAL;
+  }
+  for (int i = 0; i < g->nparts; ++i) ms[i] = i < (int)g->part_ms.size() ? g->part_ms[i] : 0.0;
+  return DFPR_OK;
 }
 
 dfpr_status dfpr_graph_free(dfpr_graph* g) {

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "../../include/dfpr.h"
 
@@ -184,6 +185,17 @@ __device__ __forceinline__ float contrib_of(float r, int d) {
   return d > 0 ? __fdiv_rn(r, (float)d) : 0.f;
 }
 
+// Graph of vertex v in a set of k graphs with vertex offsets off[0..k]
+// (binary search; off[0] = 0 <= v < off[k]).
+__device__ __forceinline__ int part_of(const int32_t* __restrict__ off, int k, int v) {
+  int lo = 0, hi = k;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 }  // namespace dfpr
 
 struct dfpr_graph {
@@ -221,6 +233,11 @@ struct dfpr_graph {
   dfpr::DevArray<uint32_t> rc_bits;       // round mode: not-converged bitmap
   dfpr::DevArray<unsigned long long> pass_ctr;  // round mode: per-pass claim counters
   dfpr::DevArray<uint32_t> item_done;     // round mode: marking items completed (helping)
+  int nparts = 1;                         // graphs in the set (disjoint union)
+  dfpr::DevArray<int32_t> part_off;       // nparts + 1 vertex offsets (when nparts > 1)
+  dfpr::DevArray<unsigned long long> part_done;  // per graph: last recomputation end (globaltimer)
+  std::vector<int32_t> part_off_host;
+  std::vector<double> part_ms;            // completion times of the last worklist update
   dfpr::DevArray<int32_t> perm;           // caller id -> internal id (when reordered)
   dfpr::DevArray<int32_t> iperm;          // internal id -> caller id
   bool relabeled = false;

@@ -193,6 +193,10 @@ struct Args {
   int32_t* job_rem;
   unsigned long long* job_sum;
   unsigned jmask;
+  // a set of graphs: vertex offsets, per-graph completion times
+  const int32_t* part_off;
+  int nparts;
+  unsigned long long* part_done;
   // numerics
   double alpha, base, tol, tol_f;
   int teleport;
@@ -205,6 +209,14 @@ struct WarpStats {
   double max_change;
   unsigned long long* prof;  // worklist: shared-memory counters (batches, 5 phases) or null
 };
+
+// (1 - alpha) / n of the graph that holds v (Eq. 1 per graph of a set).
+template <class P>
+__device__ __forceinline__ double base_of(const Args<P>& a, int v) {
+  if (a.nparts <= 1) return a.base;
+  const int p = part_of(a.part_off, a.nparts, v);
+  return (1.0 - a.alpha) / (double)(__ldg(a.part_off + p + 1) - __ldg(a.part_off + p));
+}
 
 template <class P>
 __device__ __forceinline__ bool timed_out(const Args<P>& a) {
@@ -625,13 +637,23 @@ __device__ void flush_stats(const Args<P>& a, WarpStats& st, int lane) {
   }
 }
 
-// Eq. 1 for a recomputed vertex, from its gathered sum.
+// Eq. 1 for a recomputed vertex v, from its gathered sum.
 template <class P>
 __device__ __forceinline__ typename P::val finish_rank(const Args<P>& a, typename P::acc acc,
-                                                       double dangling) {
+                                                       double dangling, int v) {
   double s = P::total(acc);
   if (a.teleport) s += dangling / (double)a.n;
-  return (typename P::val)(a.base + a.alpha * s);
+  return (typename P::val)(base_of(a, v) + a.alpha * s);
+}
+
+// Records, per graph of a set, when a warp last finished a vertex of it
+// (warp-uniform call; one atomic per distinct graph in the warp).
+template <class P>
+__device__ __forceinline__ void note_done(const Args<P>& a, int v, int lane) {
+  if (a.nparts <= 1) return;
+  const int p = v >= 0 ? part_of(a.part_off, a.nparts, v) : -1;
+  const unsigned grp = __match_any_sync(kFull, p);
+  if (p >= 0 && __ffs(grp) - 1 == lane) atomicMax(a.part_done + p, gtime());
 }
 
 // ---------------------------------------------------------------------------
@@ -649,7 +671,7 @@ __device__ __forceinline__ void vertex_epilogue(const Args<P>& a, int v, double 
                                                 bool& expand, bool& requeue, WarpStats& st) {
   double s2 = sum;
   if (a.teleport) s2 += dangling / (double)a.n;
-  const typename P::val r = (typename P::val)(a.base + a.alpha * s2);
+  const typename P::val r = (typename P::val)(base_of(a, v) + a.alpha * s2);
   typename P::val x0;
   if (e_tag != a.epoch) {
     a.ep[v] = a.epoch;
@@ -746,7 +768,9 @@ __device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk,
     vertex_epilogue(a, vv, sum, r_old, e_tag, x_prev, orow.deg, dangling, expand, requeue, st);
     free_job(a, (int)slot);
   }
-  return finish_vertices(a, vv, expand, requeue, orow, lane, s_excl, s_off, pb, st);
+  const int done = finish_vertices(a, vv, expand, requeue, orow, lane, s_excl, s_off, pb, st);
+  note_done(a, vv, lane);
+  return done;
 }
 
 // Mark token: marks one chunk of a vertex's out-row.
@@ -953,6 +977,7 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
                       requeue, st);
     phase_mark(2);
     const int done = finish_vertices(a, v, expand, requeue, orow, lane, s_excl[w], s_off[w], pb, st);
+    note_done(a, v, lane);
     phase_mark(3);
     const unsigned proc_b = __ballot_sync(kFull, v >= 0);
     if (lane == 0) {
@@ -1098,7 +1123,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
       bool expand = false;
       double dr = 0.0, thr = 0.0;
       if (v >= 0) {
-        const typename P::val r = finish_rank(a, acc, 0.0);
+        const typename P::val r = finish_rank(a, acc, 0.0, v);
         const typename P::val r_old = P::load(a.R + v);
         dr = fabs((double)r - (double)r_old);
         const int od = a.out_rows[v].deg;
@@ -1208,7 +1233,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
     const typename P::acc acc = gather(b, v, lane, s_excl[w], s_off[w], s_acc[w], st);
     bool expand = false;
     if (v >= 0) {
-      const typename P::val r = finish_rank(b, acc, dangling);
+      const typename P::val r = finish_rank(b, acc, dangling, v);
       const double dr = fabs((double)r - (double)Rin[v]);
       const int od = a.out_rows[v].deg;
       Rout[v] = r;
@@ -1345,9 +1370,15 @@ __global__ void k_fill(T* p, long long n, T v) {
 }
 
 template <class T, class CT>
-__global__ void k_init_ranks(int32_t n, const RowDesc* __restrict__ out_rows, T* R, CT* C) {
-  const T r0 = (T)(1.0 / (double)n);
+__global__ void k_init_ranks(int32_t n, const RowDesc* __restrict__ out_rows,
+                             const int32_t* __restrict__ part_off, int nparts, T* R, CT* C) {
   GRID_STRIDE(u, n) {
+    double nn = (double)n;
+    if (nparts > 1) {
+      const int p = part_of(part_off, nparts, (int)u);
+      nn = (double)(part_off[p + 1] - part_off[p]);
+    }
+    const T r0 = (T)(1.0 / nn);
     R[u] = r0;
     C[u] = contrib_of(r0, out_rows[u].deg);
   }
@@ -1458,6 +1489,9 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   a.job_rem = g->job_rem.p;
   a.job_sum = g->job_sum.p;
   a.jmask = (unsigned)g->jcap - 1u;
+  a.part_off = g->nparts > 1 ? g->part_off.p : nullptr;
+  a.nparts = g->nparts;
+  a.part_done = g->nparts > 1 ? g->part_done.p : nullptr;
   a.va_bits = g->va_bits.p;
   a.rc_bits = g->rc_bits.p;
   a.alist = g->affected_list.p;
@@ -1585,6 +1619,8 @@ dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr
     k_dangling<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, a.R, &g->ctl.p->dsum);
     DFPR_LAUNCHED();
   }
+  if (g->nparts > 1)
+    DFPR_CUDA(cudaMemsetAsync(g->part_done.p, 0, sizeof(unsigned long long) * g->nparts, s));
   const int grid = persistent_grid(g, p, (const void*)k_worklist<P>);
   DFPR_CUDA(cudaEventRecord(e0, s));  // the stats time the persistent kernel alone
   k_worklist<P><<<grid, kNT, 0, s>>>(a);
@@ -1592,6 +1628,15 @@ dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr
   DFPR_CUDA(cudaEventRecord(e1, s));
   CtlHost h = read_ctl(g);
   if (st) fill_stats(h.c, st);
+  if (g->nparts > 1 && !mark_only) {
+    std::vector<unsigned long long> done((size_t)g->nparts);
+    DFPR_CUDA(cudaMemcpyAsync(done.data(), g->part_done.p, sizeof(unsigned long long) * g->nparts,
+                              cudaMemcpyDeviceToHost, s));
+    DFPR_CUDA(cudaStreamSynchronize(s));
+    g->part_ms.assign((size_t)g->nparts, 0.0);
+    for (int i = 0; i < g->nparts; ++i)
+      if (done[i] > h.c.t_start) g->part_ms[i] = (double)(done[i] - h.c.t_start) * 1e-6;
+  }
   const bool clean = h.c.status == 0 && h.c.pending.v <= 0 && !mark_only;
   if (!clean && !mark_only) reset_worklist_state(g);
   return h.c.status ? (dfpr_status)h.c.status : DFPR_OK;
@@ -1874,9 +1919,11 @@ void alloc_iteration_state(dfpr_graph* g) {
 void reset_ranks(dfpr_graph* g) {
   cudaStream_t s = g->stream;
   if (g->cfg.precision == DFPR_FP64)
-    k_init_ranks<double, long long><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, g->C64.p);
+    k_init_ranks<double, long long><<<grid_small(g->n), kNT, 0, s>>>(
+        g->n, g->out.rows.p, g->nparts > 1 ? g->part_off.p : nullptr, g->nparts, g->R64.p, g->C64.p);
   else
-    k_init_ranks<float, float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, g->C32.p);
+    k_init_ranks<float, float><<<grid_small(g->n), kNT, 0, s>>>(
+        g->n, g->out.rows.p, g->nparts > 1 ? g->part_off.p : nullptr, g->nparts, g->R32.p, g->C32.p);
   DFPR_LAUNCHED();
 }
 

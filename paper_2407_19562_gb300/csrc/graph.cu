@@ -68,12 +68,17 @@ __device__ __forceinline__ long long upper_index(const long long* offs, long lon
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
 
 __global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                            long long m, int32_t n, int bits, unsigned long long* __restrict__ keys,
+                            long long m, int32_t n, int bits, const int32_t* __restrict__ part_off,
+                            int nparts, unsigned long long* __restrict__ keys,
                             unsigned long long* err) {
   GRID_STRIDE(i, m) {
     int a = src[i], b = dst[i];
     if (a < 0 || a >= n || b < 0 || b >= n) {
       atomicOr(err, 1ull);
+      a = 0;
+      b = 0;
+    } else if (nparts > 1 && part_of(part_off, nparts, a) != part_of(part_off, nparts, b)) {
+      atomicOr(err, 2ull);  // an edge between two graphs of a set
       a = 0;
       b = 0;
     }
@@ -415,9 +420,21 @@ __global__ void k_degree_count(const unsigned long long* __restrict__ k, long lo
   }
 }
 
-// Sort key of a vertex: decreasing degree, then increasing id.
-__global__ void k_vertex_keys(const uint32_t* __restrict__ deg, int32_t n, unsigned long long* key) {
-  GRID_STRIDE(u, n) key[u] = ((unsigned long long)(0xffffffffu - deg[u]) << 32) | (unsigned)u;
+// Sort key of a vertex: decreasing degree, then increasing id. In a set of
+// graphs the graph comes first (so each keeps its id range) and the degree is
+// clamped to 16 bits.
+__global__ void k_vertex_keys(const uint32_t* __restrict__ deg, int32_t n,
+                              const int32_t* __restrict__ part_off, int nparts,
+                              unsigned long long* key) {
+  GRID_STRIDE(u, n) {
+    if (nparts > 1) {
+      const unsigned long long part = (unsigned long long)part_of(part_off, nparts, (int)u);
+      const unsigned d = min(deg[u], 0xffffu);
+      key[u] = (part << 48) | ((unsigned long long)(0xffffu - d) << 32) | (unsigned)u;
+    } else {
+      key[u] = ((unsigned long long)(0xffffffffu - deg[u]) << 32) | (unsigned)u;
+    }
+  }
 }
 
 __global__ void k_perm_from_sorted(const unsigned long long* __restrict__ sorted, int32_t n,
@@ -691,11 +708,18 @@ void graph_build(dfpr_graph* g, const int32_t* src, const int32_t* dst, long lon
   tmp.reset((size_t)nk + 1, s);
   DFPR_CUDA(cudaMemsetAsync(words + kWErr, 0, sizeof(unsigned long long), s));
   if (m_raw > 0) {
-    k_make_keys<<<grid_for(m_raw), NT, 0, s>>>(src, dst, m_raw, n, g->bits, keys.p, words + kWErr);
+    k_make_keys<<<grid_for(m_raw), NT, 0, s>>>(src, dst, m_raw, n, g->bits,
+                                               g->nparts > 1 ? g->part_off.p : nullptr, g->nparts,
+                                               keys.p, words + kWErr);
     DFPR_LAUNCHED();
   }
-  if (read_word(g, words + kWErr, 8) != 0) {
+  const unsigned long long err = read_word(g, words + kWErr, 8);
+  if (err & 1ull) {
     set_error("dfpr_graph_load: a vertex id is outside [0, n)");
+    throw Fail{DFPR_EINVAL};
+  }
+  if (err & 2ull) {
+    set_error("dfpr_graph_load_parts: an edge joins two graphs of the set");
     throw Fail{DFPR_EINVAL};
   }
   if (loops) {
@@ -730,7 +754,8 @@ void graph_build(dfpr_graph* g, const int32_t* src, const int32_t* dst, long lon
       k_degree_count<<<grid_for(m), NT, 0, s>>>(other, m, g->bits, deg.p);
       DFPR_LAUNCHED();
     }
-    k_vertex_keys<<<grid_for(n), NT, 0, s>>>(deg.p, n, vk.p);
+    k_vertex_keys<<<grid_for(n), NT, 0, s>>>(deg.p, n, g->nparts > 1 ? g->part_off.p : nullptr,
+                                             g->nparts, vk.p);
     DFPR_LAUNCHED();
     unsigned long long* vs = radix_sort_u64(vk.p, vt.p, n, 64, sc, s);
     g->perm.reset(n, s);

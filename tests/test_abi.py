@@ -119,3 +119,21 @@ def test_oracle_and_cuda_path_are_independent():
         if f.endswith((".py", ".c", ".h")):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "import paper_2407_19562_gb300" not in text and "dfpr.h" not in text
+
+
+def test_graph_set_host_side_checks():
+    lib = dfpr.load()
+    h = ctypes.c_void_p()
+    src = np.array([0, 1], np.int32)
+    bad0 = np.array([1, 5], np.int32)       # offsets must start at 0
+    flat = np.array([0, 4, 4], np.int32)    # every graph needs a vertex
+    for off in (bad0, flat):
+        assert lib.dfpr_graph_load_parts(len(off) - 1, off.ctypes.data, 2, src.ctypes.data,
+                                         src.ctypes.data, 0, None, None, ctypes.byref(h)) == dfpr.EINVAL
+    assert lib.dfpr_graph_load_parts(0, bad0.ctypes.data, 0, None, None, 0, None, None,
+                                     ctypes.byref(h)) == dfpr.EINVAL
+    tele = dfpr.default_config(dead_end=dfpr.TELEPORT)
+    ok = np.array([0, 2, 4], np.int32)
+    assert lib.dfpr_graph_load_parts(2, ok.ctypes.data, 2, src.ctypes.data, src.ctypes.data, 0,
+                                     None, ctypes.byref(tele), ctypes.byref(h)) == dfpr.EINVAL
+    assert lib.dfpr_get_part_times(None, None) == dfpr.EINVAL
