@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat14", "grid4096", "many256"],
-                    default="rmat24")
+    ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat14", "grid4096", "many256",
+                                           "serve8"], default="rmat24")
+    ap.add_argument("--requests", type=int, default=300, help="serve8: requests per load point")
     ap.add_argument("--graphs", type=int, default=256, help="many256: number of graphs")
     ap.add_argument("--batch-frac", type=float, default=1e-4)
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
@@ -468,12 +469,118 @@ def run_many(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving loop: 8 resident R-MAT graphs (scales 18,18,19,19,20,20,21,22,
+    16 draws per vertex) receiving a Poisson stream of update batches, sizes
+    log-uniform in [10, 1e5] (80/20), graph uniform. The native server batches
+    every request admitted in a cycle into one persistent launch; the plain form
+    serves one request per cycle. Offered load: 50/80/95% of the measured
+    single-stream capacity (mean service time of requests served one by one)."""
+    import threading as th
+
+    import torch
+
+    import paper_2407_19562_gb300 as dfpr
+    torch.cuda.set_device(0)
+    scales = [18, 18, 19, 19, 20, 20, 21, 22]
+    graphs, off = [], [0]
+    for i, sc in enumerate(scales):
+        n, src, dst = workloads.rmat_graph(sc, 16, 5000 + i)
+        graphs.append((n, src, dst))
+        off.append(off[-1] + n)
+    off = np.array(off, np.int64)
+    gsrc = np.concatenate([g[1] + o for g, o in zip(graphs, off)]).astype(np.int32)
+    gdst = np.concatenate([g[2] + o for g, o in zip(graphs, off)]).astype(np.int32)
+    prec = dfpr.FP64 if args.precision == "fp64" else dfpr.FP32
+    tol = 1e-10 if args.precision == "fp64" else 1e-7
+    cfg = dfpr.default_config(precision=prec)
+    gset = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=None)
+    st0 = dfpr.static_pagerank(gset, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
+    params = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
+    u = workloads.uniform01(6000, 1, 3 * 7 * args.requests + 256)
+
+    def make_requests(k0, count):
+        reqs = []
+        for j in range(count):
+            gi = int(u[k0 + 3 * j] * len(graphs)) % len(graphs)
+            b = int(round(10.0 ** (1.0 + 4.0 * u[k0 + 3 * j + 1])))
+            n, src, dst = graphs[gi]
+            reqs.append((gi, workloads.uniform_batch(n, b, 60000 + k0 + j, src, dst)))
+        return reqs
+
+    def run_stream(reqs, gaps, slots):
+        srv = dfpr.server_create(gset, params, max_slots=slots, mem_fraction=0.5)
+        ids = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            t = t0
+            for j, (gi, batch) in enumerate(reqs):
+                t += gaps[j]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids[j] = srv.submit(gi, *batch)
+
+        thr = th.Thread(target=submitter)
+        thr.start()
+        thr.join()
+        infos = [srv.wait(r) for r in ids]
+        srv.destroy()
+        lat = [i.done_ms - i.submit_ms for i in infos]
+        span = (max(i.done_ms for i in infos) - min(i.submit_ms for i in infos)) / 1e3
+        edges = sum(len(b[0]) + len(b[2]) for _, b in reqs)
+        return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(np.mean(lat)),
+                "updates_per_s": edges / span if span > 0 else None,
+                "requests_per_s": len(reqs) / span if span > 0 else None,
+                "cycles": len({i.cycle for i in infos}),
+                "bad": sum(i.status != dfpr.OK for i in infos)}
+
+    # single-stream capacity: requests served one at a time, back to back
+    cal = make_requests(0, 40)
+    srv = dfpr.server_create(gset, params, max_slots=1)
+    svc = []
+    for gi, batch in cal:
+        r = srv.wait(srv.submit(gi, *batch))
+        svc.append(r.done_ms - r.admit_ms)
+    srv.destroy()
+    mean_svc = float(np.mean(svc))
+    points = []
+    k = 200
+    for load in (0.5, 0.8, 0.95):
+        # fresh batches for each form (a replayed batch would be all no-ops),
+        # same distribution and the same arrival times
+        reqs_b = make_requests(k, args.requests)
+        reqs_p = make_requests(k + 3 * args.requests, args.requests)
+        k += 6 * args.requests
+        rate = load / (mean_svc / 1e3)
+        rng = np.random.default_rng(int(load * 100))
+        gaps = rng.exponential(1.0 / rate, size=args.requests)
+        batched = run_stream(reqs_b, gaps, 64)
+        plain = run_stream(reqs_p, gaps, 1)
+        points.append({"load": load, "offered_req_per_s": rate, "batched": batched, "plain": plain})
+    line = {
+        "metric": "serving: per-batch p50/p99 latency (ms) and updates/s, batched vs one request per cycle",
+        "value": points[-1]["batched"]["p99_ms"], "unit": "ms (p99 at 95% load, batched)",
+        "n_gpus": 1, "higher_is_better": False,
+        "dtype": "f64" if prec == dfpr.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": "serve8: R-MAT scales 18,18,19,19,20,20,21,22; Poisson arrivals; "
+                               "batch sizes log-uniform [10,1e5], 80/20",
+                   "requests_per_point": args.requests, "mean_service_ms": mean_svc,
+                   "precision": args.precision},
+        "points": points,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "many256":
         run_many(args)
+    elif args.workload == "serve8":
+        run_serve(args)
     else:
         run_ours(args)
 

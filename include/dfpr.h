@@ -246,6 +246,52 @@ dfpr_status dfpr_initial_affected(dfpr_graph* g, uint8_t* affected, int on_devic
                                   int64_t* count);
 
 /*
+ * Serving: a server thread keeps a graph (usually a set from
+ * dfpr_graph_load_parts) resident and serves update requests: each request is
+ * one batch of edge deletions and insertions for one graph of the set. The
+ * thread runs cycles: it admits queued requests in arrival order while a slot
+ * is free (at most max_slots per cycle) and the cycle's batch memory fits in
+ * mem_fraction of the device's free memory (a cycle always admits at least one
+ * request), applies them (requests for the same graph in arrival order), then
+ * updates every affected graph with one dfpr_df_pagerank call, i.e. one
+ * persistent launch for all admitted requests. Requests that arrive during a
+ * cycle join the next one: a batch may not change a graph while an update
+ * reads it (read-only snapshot, Sec. 3.4). While the server exists, other
+ * calls on its graph return DFPR_EBUSY; dfpr_server_drain waits until it is
+ * idle. Times are host monotonic-clock ms since the server was created.
+ */
+typedef struct dfpr_server dfpr_server;
+
+typedef struct dfpr_request_info {
+  int32_t status;         /* dfpr_status of the request's cycle */
+  int32_t cycle_requests; /* requests served by the same cycle */
+  int64_t cycle;          /* index of that cycle */
+  double submit_ms;       /* when dfpr_server_submit queued it */
+  double admit_ms;        /* when its cycle started */
+  double done_ms;         /* when its cycle's update finished */
+} dfpr_request_info;
+
+dfpr_status dfpr_server_create(dfpr_graph* g, const dfpr_params* p, int32_t max_slots,
+                               double mem_fraction, dfpr_server** out);
+
+/* Queues a request for graph `part` (local ids of that graph; host arrays,
+ * copied). Thread-safe. *request_id identifies it for dfpr_server_wait.
+ * EINVAL for a bad part or id (checked here, before queueing). */
+dfpr_status dfpr_server_submit(dfpr_server* s, int32_t part, int64_t n_del,
+                               const int32_t* del_src, const int32_t* del_dst, int64_t n_ins,
+                               const int32_t* ins_src, const int32_t* ins_dst,
+                               int64_t* request_id);
+
+/* Blocks until the request is done; fills *info (may be NULL). */
+dfpr_status dfpr_server_wait(dfpr_server* s, int64_t request_id, dfpr_request_info* info);
+
+/* Blocks until every queued request is done and the server is idle. */
+dfpr_status dfpr_server_drain(dfpr_server* s);
+
+/* Drains, stops the thread and frees the server (the graph stays). */
+dfpr_status dfpr_server_destroy(dfpr_server* s);
+
+/*
  * Installs the device allocator used for all later allocations (NULL, NULL
  * restores cudaMalloc / cudaFree). alloc(bytes, stream, ctx) returns a device
  * pointer or NULL; free(ptr, bytes, stream, ctx) releases it. Memory already

@@ -27,7 +27,7 @@ __all__ = [
     "default_config", "default_params", "graph_load", "graph_free", "graph_info",
     "graph_set_stream", "apply_batch", "df_pagerank", "nd_pagerank", "static_pagerank",
     "get_ranks", "set_ranks", "get_csr", "get_csc", "initial_affected", "set_allocator",
-    "graph_load_parts", "get_part_times",
+    "graph_load_parts", "get_part_times", "Server", "RequestInfo", "server_create",
     "use_torch_allocator", "OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "EBUSY",
     "FP64", "FP32", "SELF_LOOPS", "TELEPORT", "WORKLIST", "ROUND", "JACOBI",
 ]
@@ -77,6 +77,15 @@ class Stats(ctypes.Structure):
         return d
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("cycle_requests", ctypes.c_int32),
+                ("cycle", ctypes.c_int64), ("submit_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                            ctypes.c_void_p)
@@ -105,6 +114,12 @@ def load():
                                            ctypes.POINTER(vp)]),
             "dfpr_graph_parts": (st, [vp, ctypes.POINTER(i32)]),
             "dfpr_get_part_times": (st, [vp, vp]),
+            "dfpr_server_create": (st, [vp, ctypes.POINTER(Params), i32, ctypes.c_double,
+                                        ctypes.POINTER(vp)]),
+            "dfpr_server_submit": (st, [vp, i32, i64, vp, vp, i64, vp, vp, ctypes.POINTER(i64)]),
+            "dfpr_server_wait": (st, [vp, i64, ctypes.POINTER(RequestInfo)]),
+            "dfpr_server_drain": (st, [vp]),
+            "dfpr_server_destroy": (st, [vp]),
             "dfpr_graph_free": (st, [vp]),
             "dfpr_graph_set_stream": (st, [vp, vp]),
             "dfpr_graph_info": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -420,6 +435,54 @@ def initial_affected(g: Graph, out=None):
     cnt = ctypes.c_int64()
     _check(load().dfpr_initial_affected(g.handle, p, dev, ctypes.byref(cnt)), "initial_affected")
     return out, int(cnt.value)
+
+
+class Server:
+    """dfpr_server_*: a native server thread serving update requests on a graph
+    (set). submit() queues one graph's batch (host arrays, local ids) and returns
+    a request id; wait() blocks until its cycle is done."""
+
+    def __init__(self, handle: int, graph: Graph):
+        self._h = handle
+        self.graph = graph
+
+    def submit(self, part, del_src, del_dst, ins_src, ins_dst) -> int:
+        a = [np.ascontiguousarray(x, np.int32) for x in (del_src, del_dst, ins_src, ins_dst)]
+        if len(a[0]) != len(a[1]) or len(a[2]) != len(a[3]):
+            raise DfprError(EINVAL, "server_submit", "source and target lengths differ")
+        rid = ctypes.c_int64()
+        _check(load().dfpr_server_submit(self._h, int(part), len(a[0]), a[0].ctypes.data,
+                                         a[1].ctypes.data, len(a[2]), a[2].ctypes.data,
+                                         a[3].ctypes.data, ctypes.byref(rid)), "server_submit")
+        return int(rid.value)
+
+    def wait(self, request_id: int) -> RequestInfo:
+        info = RequestInfo()
+        _check(load().dfpr_server_wait(self._h, int(request_id), ctypes.byref(info)), "server_wait")
+        return info
+
+    def drain(self):
+        _check(load().dfpr_server_drain(self._h), "server_drain")
+
+    def destroy(self):
+        h, self._h = self._h, None
+        if h:
+            _check(load().dfpr_server_destroy(h), "server_destroy")
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def server_create(g: Graph, params: Params | None = None, max_slots: int = 64,
+                  mem_fraction: float = 0.5) -> Server:
+    h = ctypes.c_void_p()
+    _check(load().dfpr_server_create(g.handle, ctypes.byref(params) if params is not None else None,
+                                     int(max_slots), float(mem_fraction), ctypes.byref(h)),
+           "server_create")
+    return Server(h.value, g)
 
 
 def set_allocator(alloc=None, free=None, ctx=None):

@@ -132,7 +132,9 @@ void check_params(const dfpr_params& p) {
 }
 
 
-dfpr_status run_call(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, RunKind kind) {
+}  // namespace
+
+dfpr_status run_update(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, RunKind kind) {
   dfpr_params p;
   if (pp) p = *pp;
   else dfpr_default_params(&p);
@@ -159,7 +161,6 @@ dfpr_status run_call(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, RunKi
   return r;
 }
 
-}  // namespace
 }  // namespace dfpr
 
 using namespace dfpr;
@@ -432,7 +433,7 @@ dfpr_status dfpr_df_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* st
   API_BEGIN
   BusyGuard bg(g);
   DeviceGuard dg(g->device);
-  return run_call(g, p, stats, kRunDF);
+  return run_update(g, p, stats, kRunDF);
   API_END
 }
 
@@ -444,7 +445,7 @@ dfpr_status dfpr_nd_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* st
   API_BEGIN
   BusyGuard bg(g);
   DeviceGuard dg(g->device);
-  return run_call(g, p, stats, kRunND);
+  return run_update(g, p, stats, kRunND);
   API_END
 }
 
@@ -456,7 +457,7 @@ dfpr_status dfpr_static_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats
   API_BEGIN
   BusyGuard bg(g);
   DeviceGuard dg(g->device);
-  return run_call(g, p, stats, kRunStatic);
+  return run_update(g, p, stats, kRunStatic);
   API_END
 }
 

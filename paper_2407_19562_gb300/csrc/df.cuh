@@ -11,6 +11,10 @@ enum RunKind { kRunDF = 0, kRunND = 1, kRunStatic = 2 };
 // ETIMEOUT); throws Fail on CUDA or argument errors.
 dfpr_status run_iteration(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st);
 
+// Checks parameters and runs one update (the body of dfpr_df_pagerank,
+// dfpr_nd_pagerank, dfpr_static_pagerank; the caller holds the graph).
+dfpr_status run_update(dfpr_graph* g, const dfpr_params* p, dfpr_stats* st, RunKind kind);
+
 // Initial marking only: affected flags (device, n bytes) and their count.
 void initial_affected(dfpr_graph* g, uint8_t* affected_dev, long long* count);
 

@@ -137,3 +137,13 @@ def test_graph_set_host_side_checks():
     assert lib.dfpr_graph_load_parts(2, ok.ctypes.data, 2, src.ctypes.data, src.ctypes.data, 0,
                                      None, ctypes.byref(tele), ctypes.byref(h)) == dfpr.EINVAL
     assert lib.dfpr_get_part_times(None, None) == dfpr.EINVAL
+
+
+def test_server_host_side_checks():
+    lib = dfpr.load()
+    h = ctypes.c_void_p()
+    assert lib.dfpr_server_create(None, None, 4, 0.5, ctypes.byref(h)) == dfpr.EINVAL
+    assert lib.dfpr_server_submit(None, 0, 0, None, None, 0, None, None, None) == dfpr.EINVAL
+    assert lib.dfpr_server_wait(None, 1, None) == dfpr.EINVAL
+    assert lib.dfpr_server_drain(None) == dfpr.EINVAL
+    assert lib.dfpr_server_destroy(None) == dfpr.OK
