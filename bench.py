@@ -17,6 +17,7 @@ core) on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -149,6 +150,29 @@ def phase_share(stats):
             tot[k] = tot.get(k, 0) + v
     all_ = sum(tot.values()) or 1
     return {k: round(v / all_, 4) for k, v in tot.items()}
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_worklist
+# launch from an ncu capture of the same workload, kept with a hash of the
+# kernel's sources: a figure is reported only while the sources are unchanged.
+MEASURED_TRAFFIC = {
+    ("rmat24-batch0.0001", "fp64", "worklist"): ("42eb3062a46a08cd", 398.37e9),
+}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("df.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2407_19562_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, precision, mode):
+    rec = MEASURED_TRAFFIC.get((workload, precision, mode))
+    if rec is None or rec[0] != kernel_source_hash():
+        return None
+    return rec[1]
 
 
 def load_peaks():
@@ -344,7 +368,9 @@ def run_ours(args):
                    "l2": "flushed by a 256 MiB write between steps (outside the events)",
                    "replicas": ws},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(f"{args.workload}-batch{args.batch_frac:g}",
+                                                 args.precision, args.mode), "peak_kind": peak_kind,
                      "kernel": "k_worklist (persistent DF kernel)",
                      "kernel_ms": float(np.mean(kern_ms)),
                      "algorithmic_bytes_per_launch": float(np.mean(bytes_per))},
