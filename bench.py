@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat14", "grid4096", "many256",
+    ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat24e4", "rmat14", "grid4096", "many256",
                                            "serve8"], default="rmat24")
     ap.add_argument("--requests", type=int, default=300, help="serve8: requests per load point")
     ap.add_argument("--graphs", type=int, default=256, help="many256: number of graphs")
@@ -60,6 +60,8 @@ def parse():
 WORKLOADS = {
     "rmat24": dict(kind="rmat", scale=24, edge_factor=16, seed=3),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=3),
+    # profile case: vectors larger than L2 (n = 16.8M) but ~2 GB on the device
+    "rmat24e4": dict(kind="rmat", scale=24, edge_factor=4, seed=3),
     "rmat14": dict(kind="rmat", scale=14, edge_factor=16, seed=1),
     "grid4096": dict(kind="grid", L=4096, seed=4),
 }

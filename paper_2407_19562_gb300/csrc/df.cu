@@ -70,6 +70,14 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
 }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
+// Release/acquire fence at GPU scope. A relaxed write after it is a release
+// of everything before it; a relaxed read before it is an acquire for
+// everything after it. It does not order a write before a later read of
+// another location, so the two places that need that (rank writes before the
+// state-word check, state change before reading contributions) keep the
+// sequentially consistent __threadfence().
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void atomic_add_ll(long long* p, long long v) {
   atomicAdd((unsigned long long*)p, (unsigned long long)v);
 }
@@ -204,11 +212,31 @@ struct Args {
   int mark_only;
 };
 
-struct WarpStats {
-  unsigned long long edges, expansions, edges_marked, pushes, affected;
-  double max_change;
-  unsigned long long* prof;  // worklist: shared-memory counters (batches, 5 phases) or null
+// Per-warp statistics: counters in shared memory that lane 0 updates with
+// warp totals (so they hold no registers), and each lane's largest change.
+enum {
+  kStEdges, kStExpansions, kStMarked, kStPushes, kStAffected,  // flushed by every kernel
+  kStBatches, kStPhase0, kStTokens = kStPhase0 + 5, kStJobs,   // worklist only
+  kStProcessed, kStClock, kStCount
 };
+struct WarpStats {
+  unsigned long long* c;  // kStCount counters of this warp (shared memory)
+  double max_change;
+};
+
+// Points st at this warp's counters and clears them (warp-uniform call).
+__device__ __forceinline__ void stats_init(WarpStats& st, unsigned long long* c, int lane) {
+  st.c = c;
+  st.max_change = 0.0;
+  if (lane < kStCount) c[lane] = 0ull;
+  __syncwarp();
+}
+
+// Adds the number of lanes with `pred` to counter k (warp-uniform call).
+__device__ __forceinline__ void stats_count(WarpStats& st, int k, bool pred, int lane) {
+  const unsigned b = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0 && b) st.c[k] += (unsigned long long)__popc(b);
+}
 
 // (1 - alpha) / n of the graph that holds v (Eq. 1 per graph of a set).
 template <class P>
@@ -252,11 +280,32 @@ __device__ __forceinline__ int owner_of(const int* s_excl, int e) {
 
 constexpr int kUnroll = 4;  // 32-edge chunks with loads in flight at once
 
+// Loads the ids of kUnroll 32-edge chunks of a warp's concatenated edge list,
+// starting at edge `base`: lane i takes edges base + 32k + i. owner[k] is the
+// lane whose row holds the edge (-1 past the end).
+__device__ __forceinline__ void load_chunk_ids(const int32_t* __restrict__ edges, const int* s_excl,
+                                               const long long* s_off, int base, int total, int lane,
+                                               int (&owner)[kUnroll], int (&id)[kUnroll]) {
+#pragma unroll
+  for (int k = 0; k < kUnroll; ++k) {
+    const int e = base + k * 32 + lane;
+    owner[k] = -1;
+    id[k] = 0;
+    if (e < total) {
+      const int o = owner_of(s_excl, e);
+      owner[k] = o;
+      id[k] = __ldg(edges + s_off[o] + (e - s_excl[o]));
+    }
+  }
+}
+
 // Warp-cooperative edge-balanced gather: lane i owns vertex v_i (or -1).
 // Returns sum_{u in in(v_i)} C[u] in lane i. The in-edges of the 32 vertices
-// are walked as one list, kUnroll chunks of 32 at a time: first every chunk's
-// ids are loaded, then every chunk's contributions, then each chunk is reduced
-// by a segmented warp scan whose segment tails add into s_acc[owner].
+// are walked as one list, kUnroll chunks of 32 at a time. The loop is
+// software-pipelined: the ids of the next kUnroll chunks are loaded while the
+// contributions of the current ones are in flight, so each step waits for one
+// memory round trip, not two. Each chunk is reduced by a segmented warp scan
+// whose segment tails add into s_acc[owner].
 template <class P>
 __device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl, long long* s_off,
                                   typename P::acc* s_acc, WarpStats& st) {
@@ -279,24 +328,15 @@ __device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl
   s_off[lane] = off;
   s_acc[lane] = P::zero();
   __syncwarp();
+  int owner[kUnroll], uid[kUnroll];
+  if (total > 0) load_chunk_ids(a.in_edges, s_excl, s_off, 0, total, lane, owner, uid);
   for (int base = 0; base < total; base += 32 * kUnroll) {
-    int owner[kUnroll];
-    int uid[kUnroll];
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int e = base + k * 32 + lane;
-      owner[k] = -1;
-      uid[k] = 0;
-      if (e < total) {
-        const int o = owner_of(s_excl, e);
-        owner[k] = o;
-        uid[k] = __ldg(a.in_edges + s_off[o] + (e - s_excl[o]));
-      }
-    }
     typename P::contrib xv[kUnroll];
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k)
       xv[k] = owner[k] >= 0 ? P::load_c(a.C + uid[k]) : (typename P::contrib)0;
+    int owner_n[kUnroll], uid_n[kUnroll];
+    load_chunk_ids(a.in_edges, s_excl, s_off, base + 32 * kUnroll, total, lane, owner_n, uid_n);
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       if (base + k * 32 >= total) break;  // warp-uniform
@@ -312,8 +352,13 @@ __device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl
       if (owner[k] >= 0 && (lane == 31 || knext != key)) s_acc[key] = P::add(s_acc[key], x);
       __syncwarp();
     }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      owner[k] = owner_n[k];
+      uid[k] = uid_n[k];
+    }
   }
-  st.edges += (unsigned long long)deg;
+  if (lane == 0) st.c[kStEdges] += (unsigned long long)total;
   return s_acc[lane];
 }
 
@@ -355,9 +400,9 @@ __device__ bool buf_flush(const Args<P>& a, PushBuf pb, int lane, WarpStats& st)
     const long long delta = (long long)nnew - (long long)*pb.owed;
     *pb.owed = 0;
     if (delta) atomic_add_ll(&a.ctl->pending.v, delta);
-    __threadfence();
+    fence_acq_rel();
     base = atomicAdd(&a.ctl->tail.v, (unsigned long long)cnt);
-    st.pushes += (unsigned long long)cnt;
+    st.c[kStPushes] += (unsigned long long)cnt;
   }
   base = __shfl_sync(kFull, base, 0);
   bool ok = true;
@@ -446,7 +491,7 @@ __device__ void push_tokens(const Args<P>& a, int cnt, unsigned kind, unsigned x
   unsigned long long base = 0;
   if (lane == 0) {
     atomic_add_ll(&a.ctl->pending.v, total);
-    __threadfence();
+    fence_acq_rel();
     base = atomicAdd(&a.ctl->ttail.v, (unsigned long long)total);
   }
   base = __shfl_sync(kFull, base, 0);
@@ -464,7 +509,7 @@ __device__ void push_tokens(const Args<P>& a, int cnt, unsigned kind, unsigned x
     }
     if (ok) *(volatile unsigned long long*)slot = make_token(kind, x, (unsigned)k);
   }
-  __threadfence();
+  fence_acq_rel();
   __syncwarp();
   if (lane == 0) atomic_add_ll(&a.ctl->tavail.v, total);
 }
@@ -529,7 +574,7 @@ __device__ void free_job(const Args<P>& a, int id) {
     __nanosleep(32);
   }
   *(volatile int*)slot = id;
-  __threadfence();
+  fence_acq_rel();
   atomic_add_ll(&a.ctl->favail.v, 1);
 }
 
@@ -554,28 +599,27 @@ __device__ void expand_rows(const Args<P>& a, int v, int od, long long oo, int l
   s_excl[lane] = incl - od;
   s_off[lane] = oo;
   __syncwarp();
+  int own[kUnroll], t[kUnroll];
+  load_chunk_ids(a.out_edges, s_excl, s_off, 0, total, lane, own, t);
   for (int base = 0; base < total; base += 32 * kUnroll) {
-    int t[kUnroll];
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int e = base + k * 32 + lane;
-      t[k] = -1;
-      if (e < total) {
-        const int o = owner_of(s_excl, e);
-        t[k] = __ldg(a.out_edges + s_off[o] + (e - s_excl[o]));
-      }
-    }
     unsigned wv[kUnroll];
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) wv[k] = t[k] >= 0 ? ld_volatile(a.state + (t[k] >> 4)) : 0u;
+    for (int k = 0; k < kUnroll; ++k) wv[k] = own[k] >= 0 ? ld_volatile(a.state + (t[k] >> 4)) : 0u;
+    int own_n[kUnroll], t_n[kUnroll];
+    load_chunk_ids(a.out_edges, s_excl, s_off, base + 32 * kUnroll, total, lane, own_n, t_n);
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       if (base + k * 32 >= total) break;  // warp-uniform
-      const bool need = mark_one(a, t[k], t[k] >= 0, wv[k]);
+      const bool need = mark_one(a, t[k], own[k] >= 0, wv[k]);
       buf_push(a, pb, t[k], need, true, lane, st);
     }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      own[k] = own_n[k];
+      t[k] = t_n[k];
+    }
   }
-  if (lane == 0) st.edges_marked += (unsigned long long)total;
+  if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
 }
 
 // Marking item: a chunk of a source's out-row, or up to 32 deletion targets.
@@ -601,39 +645,31 @@ __device__ void do_mark_item(const Args<P>& a, long long item, int lane, WarpSta
       const int t = valid ? __ldg(a.out_edges + r.off + e) : 0;
       mark(t, valid);
     }
-    if (lane == 0) st.edges_marked += (unsigned long long)max(0ll, end - beg);
+    if (lane == 0) st.c[kStMarked] += (unsigned long long)max(0ll, end - beg);
   } else {
     const long long j = (item - n_src_items) * 32 + lane;
     const bool valid = j < a.n_mark_dst;
     const int t = valid ? a.mark_dst[j] : 0;
     mark(t, valid);
-    if (lane == 0) st.edges_marked += (unsigned long long)min(32ll, a.n_mark_dst - (item - n_src_items) * 32);
+    if (lane == 0) st.c[kStMarked] += (unsigned long long)min(32ll, a.n_mark_dst - (item - n_src_items) * 32);
   }
 }
 
 template <class P>
 __device__ void flush_stats(const Args<P>& a, WarpStats& st, int lane) {
-  // every lane holds partial counts; reduce to lane 0
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    st.edges += __shfl_down_sync(kFull, st.edges, d);
-    st.expansions += __shfl_down_sync(kFull, st.expansions, d);
-    st.affected += __shfl_down_sync(kFull, st.affected, d);
+  for (int d = 16; d > 0; d >>= 1)
     st.max_change = fmax(st.max_change, __shfl_down_sync(kFull, st.max_change, d));
-  }
+  __syncwarp();
   if (lane == 0) {
     DfCtl* c = a.ctl;
-    if (st.edges) atomicAdd(&c->edges, st.edges);
-    if (st.expansions) atomicAdd(&c->expansions, st.expansions);
-    if (st.edges_marked) atomicAdd(&c->edges_marked, st.edges_marked);
-    if (st.pushes) atomicAdd(&c->pushes, st.pushes);
-    if (st.affected) atomicAdd(&c->affected, st.affected);
+    const unsigned long long* k = st.c;
+    if (k[kStEdges]) atomicAdd(&c->edges, k[kStEdges]);
+    if (k[kStExpansions]) atomicAdd(&c->expansions, k[kStExpansions]);
+    if (k[kStMarked]) atomicAdd(&c->edges_marked, k[kStMarked]);
+    if (k[kStPushes]) atomicAdd(&c->pushes, k[kStPushes]);
+    if (k[kStAffected]) atomicAdd(&c->affected, k[kStAffected]);
     if (st.max_change > 0) atomicMax(&c->max_change_bits, (unsigned long long)__double_as_longlong(st.max_change));
-    if (st.prof) {
-      if (st.prof[0]) atomicAdd(&c->batches, st.prof[0]);
-      for (int i = 0; i < 5; ++i)
-        if (st.prof[1 + i]) atomicAdd(&c->phase[i], st.prof[1 + i]);
-    }
   }
 }
 
@@ -668,15 +704,16 @@ template <class P>
 __device__ __forceinline__ void vertex_epilogue(const Args<P>& a, int v, double sum,
                                                 typename P::val r_old, uint32_t e_tag,
                                                 typename P::val x_prev, int od, double dangling,
-                                                bool& expand, bool& requeue, WarpStats& st) {
+                                                bool& expand, bool& requeue, bool& fresh,
+                                                WarpStats& st) {
   double s2 = sum;
   if (a.teleport) s2 += dangling / (double)a.n;
   const typename P::val r = (typename P::val)(base_of(a, v) + a.alpha * s2);
   typename P::val x0;
-  if (e_tag != a.epoch) {
+  fresh = e_tag != a.epoch;
+  if (fresh) {
     a.ep[v] = a.epoch;
     x0 = r_old;
-    st.affected++;
   } else {
     x0 = x_prev;
   }
@@ -689,7 +726,6 @@ __device__ __forceinline__ void vertex_epilogue(const Args<P>& a, int v, double 
   a.X[v] = expand ? r : x0;
   requeue = dr > thr;
   st.max_change = fmax(st.max_change, dr);
-  if (expand) st.expansions++;
 }
 
 // After the epilogue of lane-local vertices: marks out-neighbours of expanding
@@ -721,7 +757,7 @@ __device__ int finish_vertices(const Args<P>& a, int v, bool expand, bool requeu
 template <class P>
 __device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk, int lane,
                                 int* s_excl, long long* s_off, PushBuf pb, WarpStats& st) {
-  __threadfence();  // the job record was published before the token
+  fence_acq_rel();  // the job record was published before the token
   const int v = ld_volatile(a.job_v + slot);
   const RowDesc row = load_row(a.in_rows + v);
   const long long beg = (long long)chunk * kGatherChunk;
@@ -745,16 +781,16 @@ __device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk,
   int last = 0;
   if (lane == 0) {
     P::job_add(a.job_sum + slot, acc);
-    __threadfence();
+    fence_acq_rel();
     last = atomicSub(a.job_rem + slot, 1) == 1;
-    st.edges += (unsigned long long)max(0ll, end - beg);
+    st.c[kStEdges] += (unsigned long long)max(0ll, end - beg);
   }
   last = __shfl_sync(kFull, last, 0);
   if (!last) return 0;
   // finish the heavy vertex (lane 0 owns it)
-  __threadfence();
+  fence_acq_rel();
   const int vv = lane == 0 ? v : -1;
-  bool expand = false, requeue = false;
+  bool expand = false, requeue = false, fresh = false;
   RowDesc orow;
   orow.off = 0;
   orow.deg = 0;
@@ -765,8 +801,11 @@ __device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk,
     const typename P::val x_prev = P::load(a.X + vv);
     orow = load_row(a.out_rows + vv);
     const double dangling = a.teleport ? a.ctl->dsum : 0.0;
-    vertex_epilogue(a, vv, sum, r_old, e_tag, x_prev, orow.deg, dangling, expand, requeue, st);
+    vertex_epilogue(a, vv, sum, r_old, e_tag, x_prev, orow.deg, dangling, expand, requeue, fresh,
+                    st);
     free_job(a, (int)slot);
+    st.c[kStAffected] += fresh ? 1ull : 0ull;  // lane 0 only
+    st.c[kStExpansions] += expand ? 1ull : 0ull;
   }
   const int done = finish_vertices(a, vv, expand, requeue, orow, lane, s_excl, s_off, pb, st);
   note_done(a, vv, lane);
@@ -796,7 +835,7 @@ __device__ void run_mark_token(const Args<P>& a, unsigned u, unsigned chunk, int
       buf_push(a, pb, t[k], mark_one(a, t[k], t[k] >= 0, wv[k]), true, lane, st);
     }
   }
-  if (lane == 0) st.edges_marked += (unsigned long long)max(0ll, end - beg);
+  if (lane == 0) st.c[kStMarked] += (unsigned long long)max(0ll, end - beg);
   buf_flush(a, pb, lane, st);
 }
 
@@ -807,21 +846,20 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   __shared__ typename P::acc s_acc[kWPB][32];
   __shared__ int s_push[kWPB][kPushCap];
   __shared__ int s_pcnt[kWPB][3];
-  __shared__ unsigned long long s_prof[kWPB][6];  // batches, then cycles per phase
+  __shared__ unsigned long long s_stat[kWPB][kStCount];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   DfCtl* ctl = a.ctl;
-  WarpStats st = {};
+  WarpStats st;
+  stats_init(st, s_stat[w], lane);
   if (lane == 0) {
     s_pcnt[w][0] = 0;
     s_pcnt[w][1] = 0;
     s_pcnt[w][2] = 0;
-    for (int i = 0; i < 6; ++i) s_prof[w][i] = 0;
   }
   __syncwarp();
-  st.prof = s_prof[w];
+  unsigned long long* const sc = s_stat[w];  // lane 0: counters; kStProcessed = recomputations
+                                             // not yet added to the work-cap count
   const PushBuf pb{s_push[w], &s_pcnt[w][0], &s_pcnt[w][1], &s_pcnt[w][2]};
-  unsigned long long local_processed = 0;  // lane 0: recomputations not yet added to the cap count
-  unsigned long long local_tokens = 0, local_jobs = 0;
   auto mark = [&](int t, bool valid) {
     const unsigned word = valid ? ld_volatile(a.state + (t >> 4)) : 0u;
     const bool need = mark_one(a, t, valid, word);
@@ -845,12 +883,12 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   // Stage 2: chunk tokens first (they finish heavy vertices), then batches of
   // queued vertices, until nothing is queued, running or tokenised.
   unsigned backoff = 32;
-  long long t_prev = clock64();
+  if (lane == 0) sc[kStClock] = (unsigned long long)clock64();
   auto phase_mark = [&](int ph) {  // lane 0 charges the time since the last mark to `ph`
     if (lane == 0) {
-      const long long t = clock64();
-      s_prof[w][1 + ph] += (unsigned long long)(t - t_prev);
-      t_prev = t;
+      const unsigned long long t = (unsigned long long)clock64();
+      sc[kStPhase0 + ph] += t - sc[kStClock];
+      sc[kStClock] = t;
     }
   };
   while (!a.mark_only) {
@@ -865,8 +903,8 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       else run_mark_token(a, x, y, lane, pb, st);
       if (lane == 0) {
         *pb.owed += 1 + done;  // the token's unit (and the finished vertex's)
-        ++local_tokens;
-        local_processed += (unsigned long long)done;
+        sc[kStTokens] += 1ull;
+        sc[kStProcessed] += (unsigned long long)done;
       }
       __syncwarp();
       phase_mark(kind == 0 ? 2 : 3);
@@ -888,9 +926,9 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       settle_owed(a, pb, lane);
       int stop = 0;
       if (lane == 0) {
-        if (local_processed) {
-          atomicAdd(&ctl->processed.v, local_processed);
-          local_processed = 0;
+        if (sc[kStProcessed]) {
+          atomicAdd(&ctl->processed.v, sc[kStProcessed]);
+          sc[kStProcessed] = 0;
         }
         if (ld_volatile(&ctl->abort) || ld_volatile(&ctl->pending.v) <= 0) stop = 1;
         else if (timed_out(a)) {
@@ -905,7 +943,7 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       continue;
     }
     backoff = 32;
-    if (lane == 0) s_prof[w][0] += 1;
+    if (lane == 0) sc[kStBatches] += 1;
     h = __shfl_sync(kFull, h, 0);
     int v = -1;
     bool ok = true;
@@ -944,14 +982,14 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
             a.job_v[slot] = v;
             a.job_sum[slot] = 0ull;
             a.job_rem[slot] = nch;
-            __threadfence();
+            fence_acq_rel();
           }
         }
       }
       const unsigned jobs_b = __ballot_sync(kFull, nch > 0);
       if (jobs_b) {
         push_tokens(a, nch, 0u, (unsigned)max(slot, 0), lane, st);
-        if (lane == 0) local_jobs += (unsigned long long)__popc(jobs_b);
+        if (lane == 0) sc[kStJobs] += (unsigned long long)__popc(jobs_b);
         if (nch > 0) v = -1;
       }
     }
@@ -971,10 +1009,12 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     }
     const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
     const double dangling = a.teleport ? ctl->dsum : 0.0;
-    bool expand = false, requeue = false;
+    bool expand = false, requeue = false, fresh = false;
     if (v >= 0)
       vertex_epilogue(a, v, P::total(acc), r_old, e_tag, x_prev, orow.deg, dangling, expand,
-                      requeue, st);
+                      requeue, fresh, st);
+    stats_count(st, kStAffected, fresh, lane);
+    stats_count(st, kStExpansions, expand, lane);
     phase_mark(2);
     const int done = finish_vertices(a, v, expand, requeue, orow, lane, s_excl[w], s_off[w], pb, st);
     note_done(a, v, lane);
@@ -982,11 +1022,12 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     const unsigned proc_b = __ballot_sync(kFull, v >= 0);
     if (lane == 0) {
       *pb.owed += done;  // subtracted with the next flush or when idle
-      local_processed += (unsigned long long)__popc(proc_b);
-      if (local_processed >= 2048) {
-        const unsigned long long pr = atomicAdd(&ctl->processed.v, local_processed);
-        if ((long long)(pr + local_processed) > ctl->work_cap) stop_with(a, DFPR_ENOTCONV);
-        local_processed = 0;
+      const unsigned long long lp = sc[kStProcessed] + (unsigned long long)__popc(proc_b);
+      sc[kStProcessed] = lp;
+      if (lp >= 2048) {
+        const unsigned long long pr = atomicAdd(&ctl->processed.v, lp);
+        if ((long long)(pr + lp) > ctl->work_cap) stop_with(a, DFPR_ENOTCONV);
+        sc[kStProcessed] = 0;
       }
     }
     __syncwarp();
@@ -994,9 +1035,12 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   }
   settle_owed(a, pb, lane);
   if (lane == 0) {
-    if (local_processed) atomicAdd(&ctl->processed.v, local_processed);
-    if (local_tokens) atomicAdd(&ctl->tokens, local_tokens);
-    if (local_jobs) atomicAdd(&ctl->jobs, local_jobs);
+    if (sc[kStProcessed]) atomicAdd(&ctl->processed.v, sc[kStProcessed]);
+    if (sc[kStTokens]) atomicAdd(&ctl->tokens, sc[kStTokens]);
+    if (sc[kStJobs]) atomicAdd(&ctl->jobs, sc[kStJobs]);
+    if (sc[kStBatches]) atomicAdd(&ctl->batches, sc[kStBatches]);
+    for (int i = 0; i < 5; ++i)
+      if (sc[kStPhase0 + i]) atomicAdd(&ctl->phase[i], sc[kStPhase0 + i]);
   }
   flush_stats(a, st, lane);
 }
@@ -1033,7 +1077,9 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
   __shared__ typename P::acc s_acc[kWPB][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   DfCtl* ctl = a.ctl;
-  WarpStats st = {};
+  __shared__ unsigned long long s_stat[kWPB][kStCount];
+  WarpStats st;
+  stats_init(st, s_stat[w], lane);
   auto mark = [&](int t, bool valid) { mark_round(a, t, valid, lane); };
 
   // Marking phase with helping (Alg. 2 marking loop): claim items; then, until
@@ -1133,8 +1179,8 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         thr = P::relative ? a.tol * fabs((double)r) : a.tol;
         expand = dr > thr_f;
         st.max_change = fmax(st.max_change, dr);
-        if (expand) st.expansions++;
       }
+      stats_count(st, kStExpansions, expand, lane);
       // expansion first (with self-loops it flags v itself), then v's own flag
       {
         int od = 0;
@@ -1169,7 +1215,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
           }
           mark_round(a, t, valid, lane);
         }
-        if (lane == 0) st.edges_marked += (unsigned long long)total;
+        if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
       }
       long long conv = 0;
       if (v >= 0) {
@@ -1221,8 +1267,10 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
   __shared__ int s_excl[kWPB][32];
   __shared__ long long s_off[kWPB][32];
   __shared__ typename P::acc s_acc[kWPB][32];
+  __shared__ unsigned long long s_stat[kWPB][kStCount];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  WarpStats st = {};
+  WarpStats st;
+  stats_init(st, s_stat[w], lane);
   Args<P> b = a;
   b.C = const_cast<typename P::contrib*>(Cin);
   const long long nbatch = (count + 31) / 32;
@@ -1241,8 +1289,8 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
       const double thr_f = frontier_thr<P>(a.tol_f, r);
       expand = frontier && dr > thr_f;
       st.max_change = fmax(st.max_change, dr);
-      if (expand) st.expansions++;
     }
+    stats_count(st, kStExpansions, expand, lane);
     if (frontier) {
       int od = 0;
       long long oo = 0;
@@ -1286,7 +1334,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
         base2 = __shfl_sync(kFull, base2, 0);
         if (fresh) a.alist[base2 + __popc(bb & lanemask_lt())] = t;
       }
-      if (lane == 0) st.edges_marked += (unsigned long long)total;
+      if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
     }
     if (lane == 0) atomicAdd(&a.ctl->processed.v, (unsigned long long)min(32ll, count - bi * 32));
   }
@@ -1296,8 +1344,10 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
 // Initial marking for the Jacobi schedule: affected list + bitmap.
 template <class P>
 __global__ void __launch_bounds__(kNT) k_mark_list(Args<P> a) {
+  __shared__ unsigned long long s_stat[kWPB][kStCount];
   const int lane = threadIdx.x & 31;
-  WarpStats st = {};
+  WarpStats st;
+  stats_init(st, s_stat[threadIdx.x >> 5], lane);
   auto mark = [&](int t, bool valid) {
     bool fresh = false;
     if (valid) {
