@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["rmat24", "rmat20", "rmat24e4", "rmat14", "grid4096", "many256",
-                                           "serve8"], default="rmat24")
+                                           "serve8", "faults", "sweep", "stream"], default="rmat24")
+    ap.add_argument("--graph", choices=["rmat24", "rmat20", "rmat24e4", "grid4096"], default="rmat24",
+                    help="sweep: the graph")
     ap.add_argument("--requests", type=int, default=300, help="serve8: requests per load point")
     ap.add_argument("--graphs", type=int, default=256, help="many256: number of graphs")
     ap.add_argument("--batch-frac", type=float, default=1e-4)
@@ -601,6 +603,204 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_faults(args):
+    """Thread delays and crash-stops (Sec. 5.3, 5.4) on the GPU: one DF update
+    of R-MAT scale 20 at batch 1e-4 |E| under each fault setting, for the
+    barrier-based jacobi schedule (DF_BB), the round schedule (DF_LF, Alg. 2)
+    and the worklist schedule. A warp stands for a thread; a delay is a
+    bounded sleep after a batch of vertices, with the given probability per
+    vertex; a crash-stop warp returns at a random batch boundary. Error = L-inf
+    against the fault-free result of the same schedule."""
+    import torch
+
+    import paper_2407_19562_gb300 as dfpr
+    torch.cuda.set_device(0)
+    n, src, dst = workloads.rmat_graph(20, 16, 3)
+    tol = 1e-10
+    g = dfpr.graph_load(n, src, dst, stream=None)
+    dfpr.static_pagerank(g, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
+    R0 = dfpr.get_ranks(g)
+    m0 = g.info()["m"]
+    b = max(1, int(round(args.batch_frac * m0)))
+    batch = workloads.uniform_batch(n, b, 100, src, dst)
+    grid = 64  # CTAs: 512 warps stand for the threads
+
+    def one(mode, **kw):
+        h = dfpr.graph_load(n, src, dst, stream=None)
+        dfpr.set_ranks(h, R0)
+        dfpr.apply_batch(h, *batch)
+        p = dfpr.default_params(mode=getattr(dfpr, mode), grid_ctas=grid, timeout_ms=args.timeout_ms, **kw)
+        try:
+            st = dfpr.df_pagerank(h, p)
+        except dfpr.DfprError as e:
+            return {"status": int(e.status), "note": str(e)}, None
+        return {"status": int(st.status), "ms": st.ms, "processed": int(st.processed),
+                "passes": int(st.passes)}, dfpr.get_ranks(h)
+
+    base = {}
+    rows = []
+    for mode in ("JACOBI", "ROUND", "WORKLIST"):
+        r, R = one(mode)
+        base[mode] = R
+        rows.append({"mode": mode, "fault": "none", **r, "err": 0.0})
+    for mode in ("JACOBI", "ROUND", "WORKLIST"):
+        for prob in (1e-5, 1e-4):
+            for us in (200.0, 1000.0):
+                r, R = one(mode, fault_delay_prob=prob, fault_delay_us=us, fault_seed=1)
+                err = float(np.max(np.abs(R - base[mode]))) if R is not None else None
+                rows.append({"mode": mode, "fault": f"delay p={prob:g}/vertex {us:g}us", **r, "err": err})
+        for crashed in (1, 64, 256, 448):
+            r, R = one(mode, fault_crash_warps=crashed, fault_seed=1)
+            err = float(np.max(np.abs(R - base[mode]))) if R is not None and r["status"] == 0 else None
+            rows.append({"mode": mode, "fault": f"crash {crashed}/512 warps", **r, "err": err})
+    line = {"metric": "DF update ms/batch under simulated thread delays and crash-stops",
+            "unit": "ms/batch", "n_gpus": 1, "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"rmat20-batch{args.batch_frac:g}", "n": n, "m": m0,
+                       "batch_edges": b, "warps": grid * 8, "timeout_ms": args.timeout_ms},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_sweep(args):
+    """DF against ND and Static across batch sizes (the comparison of Sec.
+    5.2.2) on one graph: for each size 10^k |E|, k = -7 .. -1, a sequence of
+    batches; each is applied (timed) and updated by DF (timed); then the
+    previous ranks are restored and ND is timed, and Static from 1/n. The
+    sequence continues from DF's ranks. Times by CUDA events on the library's
+    stream; L2 flushed before every timed call."""
+    import torch
+
+    import paper_2407_19562_gb300 as dfpr
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spec = WORKLOADS["rmat24" if args.graph == "rmat24" else args.graph]
+    n, src, dst = make_graph(spec)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    g = dfpr.graph_load(n, src, dst, stream=stream.cuda_stream)
+    m0 = g.info()["m"]
+    tol = 1e-10
+    dfpr.static_pagerank(g, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
+    params = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    rows = []
+    reps = max(1, args.steps)
+    for k in range(-7, 0):
+        b = max(1, int(round(10.0 ** k * m0)))
+        acc = {"apply": [], "df": [], "nd": [], "static": []}
+        bad = 0
+        for i in range(reps):
+            batch = [torch.from_numpy(x).to(dev) for x in
+                     make_batch(spec, n, src, dst, b, 5000 + 100 * (k + 8) + i)]
+            torch.cuda.synchronize()
+            R_prev = dfpr.get_ranks(g)
+            t_apply, _ = timed(lambda: dfpr.apply_batch(g, *batch))
+            t_df, st = timed(lambda: dfpr.df_pagerank(g, params))
+            bad += st.status != dfpr.OK
+            R_df = dfpr.get_ranks(g)
+            dfpr.set_ranks(g, R_prev)
+            t_nd, st2 = timed(lambda: dfpr.nd_pagerank(g, params))
+            bad += st2.status != dfpr.OK
+            t_st, st3 = timed(lambda: dfpr.static_pagerank(g, params))
+            bad += st3.status != dfpr.OK
+            dfpr.set_ranks(g, R_df)
+            for key, t in (("apply", t_apply), ("df", t_df), ("nd", t_nd), ("static", t_st)):
+                acc[key].append(t)
+        med = {key: float(np.median(v)) for key, v in acc.items()}
+        rows.append({"batch_frac": 10.0 ** k, "batch_edges": b, "ms_apply": med["apply"],
+                     "ms_df": med["df"], "ms_nd": med["nd"], "ms_static": med["static"],
+                     "df_vs_nd": (med["nd"]) / (med["apply"] + med["df"]),
+                     "df_vs_static": (med["static"]) / (med["apply"] + med["df"]),
+                     "not_ok": bad})
+    line = {"metric": "DF vs ND vs Static ms per batch across batch sizes", "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.graph} batches 1e-7..1e-1 |E| (80/20)", "n": n, "m": m0,
+                       "repeats": reps, "mode": "worklist",
+                       "note": "df_vs_* = ND (or Static) update time / (apply + DF) time"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_stream(args):
+    """Insert-only updates in edge order (the protocol of Sec. 5.1.4 for the
+    temporal graphs): the first 90% of an R-MAT edge stream (scale 24, 16
+    draws per vertex, drawing order standing in for time) is loaded, then the
+    following edges arrive in batches of 1e-4 and 1e-3 of the stream. Each
+    batch: apply + DF timed; previous ranks restored, ND timed; Static timed."""
+    import torch
+
+    import paper_2407_19562_gb300 as dfpr
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n, src, dst = workloads.rmat_graph(24, 16, 3)
+    ET = len(src)
+    pre = int(0.9 * ET)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    g = dfpr.graph_load(n, src[:pre], dst[:pre], stream=stream.cuda_stream)
+    dfpr.static_pagerank(g, dfpr.default_params(mode=dfpr.JACOBI, tol=1e-13, max_iter=1000))
+    params = dfpr.default_params(tol=1e-10, timeout_ms=args.timeout_ms)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    empty = torch.zeros(0, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    rows = []
+    pos = pre
+    for frac in (1e-4, 1e-3):
+        b = int(round(frac * ET))
+        acc = {"apply": [], "df": [], "nd": [], "static": []}
+        real = []
+        bad = 0
+        for i in range(max(1, args.steps)):
+            s_ = torch.from_numpy(np.ascontiguousarray(src[pos:pos + b])).to(dev)
+            d_ = torch.from_numpy(np.ascontiguousarray(dst[pos:pos + b])).to(dev)
+            pos += b
+            torch.cuda.synchronize()
+            R_prev = dfpr.get_ranks(g)
+            t_apply, nreal = timed(lambda: dfpr.apply_batch(g, empty, empty, s_, d_))
+            real.append(int(nreal[1]))
+            t_df, st = timed(lambda: dfpr.df_pagerank(g, params))
+            R_df = dfpr.get_ranks(g)
+            dfpr.set_ranks(g, R_prev)
+            t_nd, st2 = timed(lambda: dfpr.nd_pagerank(g, params))
+            t_st, st3 = timed(lambda: dfpr.static_pagerank(g, params))
+            bad += sum(x.status != dfpr.OK for x in (st, st2, st3))
+            dfpr.set_ranks(g, R_df)
+            for key, t in (("apply", t_apply), ("df", t_df), ("nd", t_nd), ("static", t_st)):
+                acc[key].append(t)
+        med = {key: float(np.median(v)) for key, v in acc.items()}
+        rows.append({"batch_frac_of_stream": frac, "batch_edges": b,
+                     "new_edges_median": int(np.median(real)), "ms_apply": med["apply"],
+                     "ms_df": med["df"], "ms_nd": med["nd"], "ms_static": med["static"],
+                     "df_vs_nd": med["nd"] / (med["apply"] + med["df"]),
+                     "df_vs_static": med["static"] / (med["apply"] + med["df"]), "not_ok": bad})
+    line = {"metric": "insert-only stream: DF vs ND vs Static ms per batch", "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "R-MAT scale 24 edge stream, 90% preloaded, insert-only batches",
+                       "n": n, "stream_edges": ET, "repeats": max(1, args.steps), "mode": "worklist"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -609,6 +809,12 @@ def main():
         run_many(args)
     elif args.workload == "serve8":
         run_serve(args)
+    elif args.workload == "faults":
+        run_faults(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
+    elif args.workload == "stream":
+        run_stream(args)
     else:
         run_ours(args)
 

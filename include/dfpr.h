@@ -102,6 +102,29 @@ typedef struct dfpr_params {
   int32_t normalize;   /* 1: rescale ranks to sum 1 (FP64 sum) after convergence */
   int32_t grid_ctas;   /* persistent grid size; 0 = one wave on every SM */
   double timeout_ms;   /* wall-clock budget on the device; <= 0 means 60000 */
+  /* Simulated faults (Sec. 5.1.6; experiments of Sec. 5.3 and 5.4). All 0 by
+     default. A warp stands for one of the paper's threads; every draw comes
+     from a counter-based hash of fault_seed, so a run is reproducible.
+     - Thread delay: after a warp finishes the rank computation of a batch of
+       vertices, it sleeps fault_delay_us microseconds with probability
+       1 - (1 - fault_delay_prob)^k, k = the vertices in the batch, i.e.
+       fault_delay_prob per vertex. The sleep is a bounded loop of
+       __nanosleep that also ends when timeout_ms runs out.
+     - Crash-stop: fault_crash_warps warps of the launch (chosen by the hash)
+       stop taking part at a random batch boundary, without finishing any
+       bookkeeping, like a thread that never runs again. The round schedule
+       (Alg. 2) finishes without them: its passes and R_C flags let the
+       other warps recompute what they left. The worklist schedule keeps a
+       global count of open work that a crashed warp leaves unbalanced, so
+       it stops at timeout_ms with DFPR_ETIMEOUT (valid, partly updated
+       ranks). The jacobi schedule rejects crashes with DFPR_EINVAL: its
+       iteration barrier could never complete (Sec. 5.4).
+     Limits: 0 <= fault_delay_prob <= 1, 0 <= fault_delay_us <= 1e6,
+     0 <= fault_crash_warps < the warps of the launch. */
+  double fault_delay_prob;
+  double fault_delay_us;
+  int32_t fault_crash_warps;
+  uint32_t fault_seed;
 } dfpr_params;
 
 /* Counters of one call. */

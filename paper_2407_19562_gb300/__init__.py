@@ -56,7 +56,9 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tol", ctypes.c_double),
                 ("frontier_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("normalize", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_double)]
+                ("grid_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
+                ("fault_delay_prob", ctypes.c_double), ("fault_delay_us", ctypes.c_double),
+                ("fault_crash_warps", ctypes.c_int32), ("fault_seed", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):

@@ -129,6 +129,14 @@ void check_params(const dfpr_params& p) {
   DFPR_REQUIRE(p.mode >= DFPR_MODE_WORKLIST && p.mode <= DFPR_MODE_JACOBI, DFPR_EINVAL,
                "unknown mode");
   DFPR_REQUIRE(p.grid_ctas >= 0, DFPR_EINVAL, "grid_ctas must be >= 0");
+  DFPR_REQUIRE(p.fault_delay_prob >= 0.0 && p.fault_delay_prob <= 1.0, DFPR_EINVAL,
+               "fault_delay_prob must lie in [0, 1]");
+  DFPR_REQUIRE(p.fault_delay_us >= 0.0 && p.fault_delay_us <= 1e6, DFPR_EINVAL,
+               "fault_delay_us must lie in [0, 1e6]");
+  DFPR_REQUIRE(p.fault_crash_warps >= 0, DFPR_EINVAL, "fault_crash_warps must be >= 0");
+  DFPR_REQUIRE(!(p.fault_crash_warps > 0 && p.mode == DFPR_MODE_JACOBI), DFPR_EINVAL,
+               "crash-stop faults need a lock-free schedule: the jacobi schedule's iteration "
+               "barrier would never complete (Sec. 5.4)");
 }
 
 
@@ -204,6 +212,10 @@ void dfpr_default_params(dfpr_params* p) {
   p->normalize = 0;
   p->grid_ctas = 0;
   p->timeout_ms = 60000.0;
+  p->fault_delay_prob = 0.0;
+  p->fault_delay_us = 0.0;
+  p->fault_crash_warps = 0;
+  p->fault_seed = 0u;
 }
 
 int32_t dfpr_version(void) { return 100; }

@@ -210,6 +210,15 @@ struct Args {
   int teleport;
   unsigned long long timeout_ns;
   int mark_only;
+  // simulated faults (Sec. 5.1.6): per-vertex delay probability as a 64-bit
+  // threshold, delay length, crashing warps = those whose slot in a seeded
+  // permutation of the launch's warps is below fault_crash_warps
+  unsigned long long fault_seed;
+  unsigned long long fault_delay_thr;
+  unsigned long long fault_delay_ns;
+  unsigned long long fault_perm_a, fault_perm_b;
+  unsigned long long fault_warps;
+  int fault_crash_warps;
 };
 
 // Per-warp statistics: counters in shared memory that lane 0 updates with
@@ -249,6 +258,54 @@ __device__ __forceinline__ double base_of(const Args<P>& a, int v) {
 template <class P>
 __device__ __forceinline__ bool timed_out(const Args<P>& a) {
   return gtime() - a.ctl->t_start > a.timeout_ns;
+}
+
+// ---------------------------------------------------------------------------
+// Simulated thread delays and crash-stops (Sec. 5.1.6)
+// ---------------------------------------------------------------------------
+
+// SplitMix64 finaliser (Steele, Lea, Flood 2014): a counter-based hash.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+constexpr unsigned long long kCrashHorizon = 64;  // a crashing warp stops within its first 64 batches
+
+__device__ __forceinline__ unsigned long long fault_warp_id() {
+  return (unsigned long long)blockIdx.x * kWPB + (threadIdx.x >> 5);
+}
+
+// True when this warp is one of the crashing ones and its batch number k is
+// its crash point (a crash-stop: the caller returns at once, leaving any
+// bookkeeping undone).
+template <class P>
+__device__ __forceinline__ bool fault_crash(const Args<P>& a, unsigned long long k) {
+  if (a.fault_crash_warps == 0) return false;
+  const unsigned long long gid = fault_warp_id();
+  const unsigned long long slot = (gid * a.fault_perm_a + a.fault_perm_b) % a.fault_warps;
+  return slot < (unsigned long long)a.fault_crash_warps &&
+         k == mix64(a.fault_seed ^ mix64(gid)) % kCrashHorizon;
+}
+
+// Thread delay after a warp's batch number k (warp-uniform call; has_vertex:
+// this lane recomputed a vertex in it): with probability fault_delay_prob per
+// vertex the warp sleeps fault_delay_ns, in a bounded loop that also ends at
+// the time budget.
+template <class P>
+__device__ __forceinline__ void fault_delay(const Args<P>& a, unsigned long long k, bool has_vertex,
+                                           int lane) {
+  if (a.fault_delay_thr == 0ull) return;
+  const unsigned long long h = mix64(a.fault_seed ^ mix64(fault_warp_id()) ^ 0x6a09e667f3bcc909ull);
+  const bool hit = has_vertex && mix64(h + (k << 5) + (unsigned long long)lane) < a.fault_delay_thr;
+  if (!__any_sync(kFull, hit)) return;
+  const unsigned long long t0 = gtime();
+  while (gtime() - t0 < a.fault_delay_ns) {
+    if (gtime() - a.ctl->t_start > a.timeout_ns) break;
+    __nanosleep(100000);
+  }
 }
 
 template <class P>
@@ -967,6 +1024,9 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       }
     }
     if (!__all_sync(kFull, ok)) break;
+    if (a.fault_crash_warps &&
+        fault_crash(a, __shfl_sync(kFull, lane == 0 ? sc[kStBatches] : 0ull, 0)))
+      return;  // crash-stop holding claimed vertices (Sec. 5.4)
     __threadfence();  // state change before reading neighbours' contributions
 
     // Heavy in-rows become jobs of gather tokens that any warp can take; the
@@ -1032,6 +1092,8 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     }
     __syncwarp();
     phase_mark(4);
+    if (a.fault_delay_thr)
+      fault_delay(a, __shfl_sync(kFull, lane == 0 ? sc[kStBatches] : 0ull, 0), v >= 0, lane);
   }
   settle_owed(a, pb, lane);
   if (lane == 0) {
@@ -1130,6 +1192,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
 
   // Passes (Alg. 2 iteration loop).
   int pass = 0;
+  unsigned long long fk = 0;  // chunks this warp has taken (fault simulation)
   for (; pass < a.max_iter; ++pass) {
     while (true) {
       unsigned long long c = 0;
@@ -1157,6 +1220,7 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         if (!ok) v = -1;
       }
       if (!__all_sync(kFull, ok)) break;
+      if (fault_crash(a, fk)) return;  // crash-stop holding a claimed chunk (Sec. 5.4)
       // Exclusion: a vertex another warp is recomputing right now (a warp in
       // a neighbouring pass) is skipped, so a result computed from older
       // neighbour ranks never overwrites a fresher one.
@@ -1235,6 +1299,8 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         const int cnt = (int)min(32ll, len - (long long)c);
         atomicAdd(&ctl->processed.v, (unsigned long long)cnt);
       }
+      fault_delay(a, fk, v >= 0, lane);
+      ++fk;
     }
     int stop = 0;
     if (lane == 0) {
@@ -1337,6 +1403,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
       if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
     }
     if (lane == 0) atomicAdd(&a.ctl->processed.v, (unsigned long long)min(32ll, count - bi * 32));
+    fault_delay(a, (unsigned long long)bi, v >= 0, lane);
   }
   flush_stats(a, st, lane);
 }
@@ -1517,6 +1584,14 @@ unsigned grid_small(long long n) { return blocks_for(n, kNT, 152u * 16u); }
 // Host drivers
 // ---------------------------------------------------------------------------
 
+// SplitMix64 finaliser on the host (seeds the device-side fault draws).
+unsigned long long host_mix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
 template <class P>
 Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   Args<P> a;
@@ -1555,7 +1630,29 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   a.teleport = g->cfg.dead_end == DFPR_TELEPORT;
   const double tmo = p.timeout_ms > 0 ? p.timeout_ms : 60000.0;
   a.timeout_ns = (unsigned long long)(tmo * 1e6);
+  a.fault_seed = host_mix64(0x243f6a8885a308d3ull ^ (unsigned long long)p.fault_seed);
+  a.fault_delay_thr = p.fault_delay_prob >= 1.0 ? ~0ull
+                      : (unsigned long long)(p.fault_delay_prob * 18446744073709551616.0);
+  a.fault_delay_ns = (unsigned long long)(p.fault_delay_us * 1000.0);
+  a.fault_crash_warps = p.fault_crash_warps;
+  a.fault_perm_a = 1;
+  a.fault_perm_b = 0;
+  a.fault_warps = 1;
   return a;
+}
+
+// The crashing warps of a launch of `grid` CTAs: slot(w) = (w * A + B) mod W is
+// a bijection of the W warps when gcd(A, W) = 1; warps with slot < the crash
+// count crash.
+template <class P>
+void set_fault_warps(Args<P>& a, int grid) {
+  const unsigned long long W = (unsigned long long)grid * kWPB;
+  a.fault_warps = W;
+  if (a.fault_crash_warps == 0) return;  // run_any checked fault_crash_warps < W
+  unsigned long long A = (host_mix64(a.fault_seed ^ 1ull) % W) | 1ull;
+  while (std::gcd(A, W) != 1ull) A = (A + 2) % W;
+  a.fault_perm_a = A;
+  a.fault_perm_b = host_mix64(a.fault_seed ^ 2ull) % W;
 }
 
 template <class P>
@@ -1580,6 +1677,17 @@ int persistent_grid(dfpr_graph* g, const dfpr_params& p, const void* kernel) {
       per_sm < 1)
     per_sm = 1;
   return per_sm * g->sm_count;
+}
+
+// Grid of the round schedule. One CTA per 1024 vertices at most: with many
+// more warps than 32-vertex chunks per pass, idle warps would start later
+// passes while earlier ones are still being computed, using up the pass
+// budget without progress.
+template <class P>
+int round_grid(dfpr_graph* g, const dfpr_params& p) {
+  const int grid = persistent_grid(g, p, (const void*)k_round<P>);
+  if (p.grid_ctas > 0) return grid;
+  return (int)std::max<long long>(1, std::min<long long>(grid, (g->n + 1023) / 1024));
 }
 
 // Prepares marking items for the pending change set; returns the device
@@ -1673,6 +1781,7 @@ dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr
     DFPR_CUDA(cudaMemsetAsync(g->part_done.p, 0, sizeof(unsigned long long) * g->nparts, s));
   const int grid = persistent_grid(g, p, (const void*)k_worklist<P>);
   DFPR_CUDA(cudaEventRecord(e0, s));  // the stats time the persistent kernel alone
+  set_fault_warps(a, grid);
   k_worklist<P><<<grid, kNT, 0, s>>>(a);
   DFPR_LAUNCHED();
   DFPR_CUDA(cudaEventRecord(e1, s));
@@ -1723,11 +1832,8 @@ dfpr_status run_round(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_st
                                                   g->affected_list.p, g->ctl.p);
     DFPR_LAUNCHED();
   }
-  // One CTA per 1024 vertices at most: with many more warps than 32-vertex
-  // chunks per pass, idle warps would start later passes while earlier ones
-  // are still being computed, using up the pass budget without progress.
-  int grid = persistent_grid(g, p, (const void*)k_round<P>);
-  if (p.grid_ctas <= 0) grid = (int)std::max<long long>(1, std::min<long long>(grid, (g->n + 1023) / 1024));
+  const int grid = round_grid<P>(g, p);
+  set_fault_warps(a, grid);
   k_round<P><<<grid, kNT, 0, s>>>(a);
   DFPR_LAUNCHED();
   DFPR_CUDA(cudaEventRecord(e1, s));
@@ -1819,6 +1925,7 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
     count = (long long)read_word(g, &g->ctl.p->len.v, sizeof(long long));
   }
   const int grid = persistent_grid(g, p, (const void*)k_jacobi<P>);
+  const unsigned long long fault_seed0 = a.fault_seed;
   int it = 0;
   double last = 0.0;
   bool converged = false;
@@ -1829,6 +1936,7 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
       k_dangling<V><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, a.R, &g->ctl.p->dsum);
       DFPR_LAUNCHED();
     }
+    a.fault_seed = host_mix64(fault_seed0 + (unsigned long long)it);  // fresh delay draws per iteration
     k_jacobi<P><<<grid, kNT, 0, s>>>(a, a.R, a.C, R2, C2, df ? g->affected_list.p : nullptr, count,
                                      df ? 1 : 0);
     DFPR_LAUNCHED();
@@ -1897,6 +2005,12 @@ dfpr_status run_any(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stat
       cudaEventDestroy(b);
     }
   } guard{e0, e1};
+  if (p.fault_crash_warps > 0) {  // checked before any device work
+    const int grid = p.mode == DFPR_MODE_WORKLIST ? persistent_grid(g, p, (const void*)k_worklist<P>)
+                                                  : round_grid<P>(g, p);
+    DFPR_REQUIRE((long long)p.fault_crash_warps < (long long)grid * kWPB, DFPR_EINVAL,
+                 "fault_crash_warps must be below the number of warps of the launch");
+  }
   if (kind == kRunStatic) reset_ranks(g);
   g->epoch += 1;
   if (g->epoch == 0) {  // wrapped: clear epochs so that no vertex looks current
