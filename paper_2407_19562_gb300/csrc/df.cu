@@ -335,7 +335,11 @@ __device__ __forceinline__ int owner_of(const int* s_excl, int e) {
   return lo;
 }
 
-constexpr int kUnroll = 4;  // 32-edge chunks with loads in flight at once
+// 32-edge chunks whose loads are in flight at once per warp. Measured on
+// R-MAT scale 24: 2 chunks beat 4 (about 131 vs 147 ms per update), and 6 or
+// 8 were slower still. The random contribution reads oversubscribe the
+// memory system well before per-warp concurrency runs out.
+constexpr int kUnroll = 2;
 
 // Loads the ids of kUnroll 32-edge chunks of a warp's concatenated edge list,
 // starting at edge `base`: lane i takes edges base + 32k + i. owner[k] is the
