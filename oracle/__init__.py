@@ -88,6 +88,8 @@ def _load():
             lib.orc_static_lf.argtypes = [vp, vp, dbl, dbl, ci, vp, PS]
             lib.orc_initial_affected.argtypes = [vp, vp]
             lib.orc_df_bb.argtypes = [vp, vp, dbl, dbl, dbl, ci, vp, PS, vp, ci]
+            lib.orc_df_bb_teleport.argtypes = [vp, vp, dbl, dbl, dbl, dbl, ci, vp, PS]
+            lib.orc_dangling_mass.argtypes = [vp, vp, vp]
             lib.orc_df_lf.argtypes = [vp, vp, dbl, dbl, dbl, ci, vp, PS]
             lib.orc_sample_rows.argtypes = [i32, i64, vp, vp, ci, i64, vp, vp, i64, vp, vp, ci,
                                             i32, vp, vp, vp, i64]
@@ -216,6 +218,24 @@ class Graph:
         _check(self._lib.orc_df_bb(self._h, _ptr(rp), alpha, tol, tol_f, max_iter, _ptr(R),
                                    ctypes.byref(st), _ptr(tr), trace), "df_bb")
         return (R, _stats(st), tr) if trace > 0 else (R, _stats(st))
+
+    def dangling_mass(self, R):
+        """D = sum of R over dead ends (vertices without out-edges)."""
+        d = ctypes.c_double()
+        r = np.ascontiguousarray(R, np.float64)
+        _check(self._lib.orc_dangling_mass(self._h, _ptr(r), ctypes.byref(d)), "dangling_mass")
+        return d.value
+
+    def df_bb_teleport(self, R_prev, D_before, alpha=ALPHA, tol=TOL, tol_f=None, max_iter=MAX_ITER):
+        """DF_BB (Alg. 1) with the teleport reading of dead ends; D_before is the
+        dead-end mass of R_prev on the graph before the batch."""
+        tol_f = tol / 1000.0 if tol_f is None else tol_f
+        R = np.empty(self.n, np.float64)
+        st = _Stats()
+        rp = np.ascontiguousarray(R_prev, np.float64)
+        _check(self._lib.orc_df_bb_teleport(self._h, _ptr(rp), D_before, alpha, tol, tol_f, max_iter,
+                                            _ptr(R), ctypes.byref(st)), "df_bb_teleport")
+        return R, _stats(st)
 
     def df_lf(self, R_prev, alpha=ALPHA, tol=TOL, tol_f=None, max_iter=MAX_ITER):
         """DF_LF (Alg. 2) on one thread, ascending vertex order."""

@@ -469,6 +469,79 @@ int orc_df_bb(const orc_graph* gt, const double* R_prev, double alpha, double to
 }
 
 /*
+ * Dead-end mass D = sum of R[u] over vertices u with no out-edges (the
+ * teleport reading of Sec. 5.1.3).
+ */
+int orc_dangling_mass(const orc_graph* g, const double* R, double* D) {
+  if (!g || !R || !D) return ORC_EINVAL;
+  *D = dangling_mass(g, R);
+  return ORC_OK;
+}
+
+/*
+ * DF_BB (Alg. 1) with the teleport reading of dead ends (the paper's runs
+ * add self-loops instead, Sec. 5.1.3, and give no formula for this case).
+ * Every recomputed rank gets alpha * D / n, D the dead-end mass of the
+ * current ranks, taken at the start of each iteration. A vertex outside the
+ * affected set keeps a rank computed with an older D, so the frontier rule
+ * is extended to the shared term: when alpha * |D - D_last| / n > tol_f,
+ * every vertex is affected from this iteration on and D_last becomes D.
+ * D_last starts at D_before, the dead-end mass of R_prev on G^{t-1} (the D
+ * that R_prev was computed with), so a batch that moves rank into or out of
+ * dead ends by more than that bound recomputes every vertex at once.
+ * Otherwise the steps are those of orc_df_bb.
+ */
+int orc_df_bb_teleport(const orc_graph* gt, const double* R_prev, double D_before, double alpha,
+                       double tol, double tol_f, int max_iter, double* R_out, orc_stats* st) {
+  if (!gt || !R_prev || !R_out || max_iter < 0) return ORC_EINVAL;
+  int32_t n = gt->n;
+  double* R = (double*)malloc(sizeof(double) * (size_t)n);
+  double* Rn = (double*)malloc(sizeof(double) * (size_t)n);
+  uint8_t* VA = (uint8_t*)calloc((size_t)n, 1);
+  uint8_t* VAn = (uint8_t*)calloc((size_t)n, 1);
+  if (!R || !Rn || !VA || !VAn) { free(R); free(Rn); free(VA); free(VAn); return ORC_ENOMEM; }
+  orc_stats s;
+  memset(&s, 0, sizeof s);
+  memcpy(R, R_prev, sizeof(double) * (size_t)n);
+  memcpy(Rn, R_prev, sizeof(double) * (size_t)n);
+  mark_initial(gt, VA, NULL, NULL);
+  double D_last = D_before;
+  for (int i = 0; i < max_iter; ++i) {
+    double D = dangling_mass(gt, R);
+    if (alpha * fabs(D - D_last) / (double)n > tol_f) {
+      for (int32_t v = 0; v < n; ++v) VA[v] = 1;
+      D_last = D;
+    }
+    memcpy(VAn, VA, (size_t)n);
+    for (int32_t v = 0; v < n; ++v) {
+      if (!VA[v]) continue;
+      double r = rank_of(gt, R, v, alpha, D, 1, &s);
+      double dr = fabs(r - R[v]);
+      Rn[v] = r;
+      if (dr > tol_f)
+        for (int64_t e = gt->out_off[v]; e < gt->out_off[v + 1]; ++e) VAn[gt->out_idx[e]] = 1;
+    }
+    double dR = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      double d = fabs(Rn[v] - R[v]);
+      if (d > dR) dR = d;
+    }
+    double* t = R; R = Rn; Rn = t;
+    memcpy(VA, VAn, (size_t)n);
+    s.iterations = i + 1;
+    s.last_delta = dR;
+    if (dR <= tol) { s.converged = 1; break; }
+  }
+  int32_t a = 0;
+  for (int32_t v = 0; v < n; ++v) a += VA[v];
+  s.affected = a;
+  memcpy(R_out, R, sizeof(double) * (size_t)n);
+  free(R); free(Rn); free(VA); free(VAn);
+  if (st) *st = s;
+  return ORC_OK;
+}
+
+/*
  * DF_LF (Alg. 2) on a single thread. The marking phase checks each source
  * once (flag C); then each pass visits the affected vertices in ascending id,
  * updating R in place. A vertex whose change exceeds tol_f marks its

@@ -30,6 +30,10 @@ MUTATIONS = {
                                 "Rn[v] = rank_of(g, Rn, v, alpha, D, dead_end, &s);"),
     "df_bb_reads_new_vector": ("      double r = rank_of(gt, R, v, alpha, 0.0, 0, &s);",
                                "      double r = rank_of(gt, Rn, v, alpha, 0.0, 0, &s);"),
+    "teleport_df_ignores_dead_end_mass_change": ("    if (alpha * fabs(D - D_last) / (double)n > tol_f) {",
+                                                 "    if (0) {"),
+    "teleport_df_drops_dead_end_term": ("      double r = rank_of(gt, R, v, alpha, D, 1, &s);",
+                                        "      double r = rank_of(gt, R, v, alpha, 0.0, 1, &s);"),
 }
 
 

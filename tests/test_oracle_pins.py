@@ -167,6 +167,70 @@ def test_teleport_reading_matches_dense_solve(seed):
     assert abs(R.sum() - 1.0) < 1e-12
 
 
+def teleport_case(seed, change_dead_ends):
+    """A graph without self-loops and with dead ends, and a batch. With
+    change_dead_ends the batch deletes every out-edge of a vertex (a new dead
+    end) and inserts an edge out of an old dead end; otherwise it only adds
+    edges between vertices that already have out-edges."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(20, 60))
+    src, dst = random_graph(n, 0.08, rng)
+    A = adjacency(n, src, dst, self_loops=False)
+    A[0, :] = False                       # vertex 0 is a dead end
+    A[1, :] = False
+    A[1, 2] = True                        # vertex 1 has one out-edge
+    A[np.arange(n), np.arange(n)] = False
+    s, d = edges_of(A)
+    live = [u for u in range(2, n) if A[u].any()]
+    ins = []
+    while len(ins) < 3:
+        u, v = int(rng.choice(live)), int(rng.integers(0, n))
+        if u != v and not A[u, v]:
+            ins.append((u, v))
+    dels = []
+    if change_dead_ends:
+        dels = [(1, 2)]                   # vertex 1 becomes a dead end
+        ins.append((0, 3))                # vertex 0 is a dead end no more
+    B = A.copy()
+    for u, v in dels:
+        B[u, v] = False
+    for u, v in ins:
+        B[u, v] = True
+    arr = lambda pairs, k: np.array([p[k] for p in pairs], np.int32)  # noqa: E731
+    batch = (arr(dels, 0), arr(dels, 1), arr(ins, 0), arr(ins, 1))
+    return n, s, d, A, B, batch
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("change_dead_ends", [False, True])
+def test_teleport_df_bb_matches_dense_solve(seed, change_dead_ends):
+    n, s, d, A, B, batch = teleport_case(seed, change_dead_ends)
+    g0 = oracle.Graph.build(n, s, d, False)
+    R0, _ = g0.reference(dead_end=1)
+    assert np.max(np.abs(R0 - dense_pagerank(A, teleport=True))) < 1e-13
+    g1, _ = g0.apply(*batch)
+    D_before = g0.dangling_mass(R0)
+    assert abs(D_before - R0[~A.any(axis=1)].sum()) < 1e-15
+    R1, st = g1.df_bb_teleport(R0, D_before)
+    assert st.converged
+    exact = dense_pagerank(B, teleport=True)
+    assert np.max(np.abs(R1 - exact)) < 1e-9
+    if change_dead_ends:
+        # rank moved into and out of dead ends by far more than n * tol_f / alpha:
+        # the shared term changed for every vertex, so every vertex is recomputed
+        assert st.affected == n
+
+
+def test_teleport_df_bb_without_change_is_identity():
+    n, s, d, A, _, _ = teleport_case(0, False)
+    g0 = oracle.Graph.build(n, s, d, False)
+    R0, _ = g0.reference(dead_end=1)
+    empty = np.zeros(0, np.int32)
+    g1, _ = g0.apply(empty, empty, empty, empty)
+    R1, st = g1.df_bb_teleport(R0, g0.dangling_mass(R0))
+    assert st.affected == 0 and np.array_equal(R1, R0)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_lock_free_static_matches_dense_solve(seed):
     rng = np.random.default_rng(200 + seed)
