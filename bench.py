@@ -683,6 +683,7 @@ def run_sweep(args):
     tol = 1e-10
     dfpr.static_pagerank(g, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
     params = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
+    pjac = dfpr.default_params(tol=tol, mode=dfpr.JACOBI, timeout_ms=args.timeout_ms)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def timed(fn):
@@ -698,7 +699,7 @@ def run_sweep(args):
     reps = max(1, args.steps)
     for k in range(-7, 0):
         b = max(1, int(round(10.0 ** k * m0)))
-        acc = {"apply": [], "df": [], "nd": [], "static": []}
+        acc = {"apply": [], "df": [], "nd": [], "static": [], "nd_bb": [], "static_bb": []}
         bad = 0
         for i in range(reps):
             batch = [torch.from_numpy(x).to(dev) for x in
@@ -714,20 +715,29 @@ def run_sweep(args):
             bad += st2.status != dfpr.OK
             t_st, st3 = timed(lambda: dfpr.static_pagerank(g, params))
             bad += st3.status != dfpr.OK
+            # the paper's barrier-based forms: every vertex, every iteration
+            dfpr.set_ranks(g, R_prev)
+            t_ndbb, st4 = timed(lambda: dfpr.nd_pagerank(g, pjac))
+            t_stbb, st5 = timed(lambda: dfpr.static_pagerank(g, pjac))
+            bad += (st4.status != dfpr.OK) + (st5.status != dfpr.OK)
             dfpr.set_ranks(g, R_df)
-            for key, t in (("apply", t_apply), ("df", t_df), ("nd", t_nd), ("static", t_st)):
+            for key, t in (("apply", t_apply), ("df", t_df), ("nd", t_nd), ("static", t_st),
+                           ("nd_bb", t_ndbb), ("static_bb", t_stbb)):
                 acc[key].append(t)
         med = {key: float(np.median(v)) for key, v in acc.items()}
         rows.append({"batch_frac": 10.0 ** k, "batch_edges": b, "ms_apply": med["apply"],
                      "ms_df": med["df"], "ms_nd": med["nd"], "ms_static": med["static"],
+                     "ms_nd_bb": med["nd_bb"], "ms_static_bb": med["static_bb"],
                      "df_vs_nd": (med["nd"]) / (med["apply"] + med["df"]),
                      "df_vs_static": (med["static"]) / (med["apply"] + med["df"]),
+                     "df_vs_nd_bb": med["nd_bb"] / (med["apply"] + med["df"]),
+                     "df_vs_static_bb": med["static_bb"] / (med["apply"] + med["df"]),
                      "not_ok": bad})
     line = {"metric": "DF vs ND vs Static ms per batch across batch sizes", "unit": "ms",
             "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.graph} batches 1e-7..1e-1 |E| (80/20)", "n": n, "m": m0,
-                       "repeats": reps, "mode": "worklist",
-                       "note": "df_vs_* = ND (or Static) update time / (apply + DF) time"},
+                       "repeats": reps, "mode": "worklist (DF, ND, Static); jacobi (ND_BB, Static_BB)",
+                       "note": "df_vs_* = that method's update time / (apply + DF) time"},
             "rows": rows}
     print(json.dumps(line), flush=True)
 

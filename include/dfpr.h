@@ -60,7 +60,16 @@ enum {
   DFPR_SELF_LOOPS = 0, /* a self-loop on every vertex, kept through every batch
                           (Sec. 5.1.3, Sec. 5.1.4); deleting a self-loop is a no-op */
   DFPR_TELEPORT = 1    /* no self-loops added; the rank of dead ends is spread
-                          uniformly (alpha * D / n added to every vertex) */
+                          uniformly (alpha * D / n added to every vertex, D the
+                          FP64 sum of dead-end ranks, recomputed every
+                          iteration). Jacobi schedule only. In a DF update the
+                          frontier rule covers the shared term: when D differs
+                          by more than tol_f * n / alpha from the D that the
+                          unaffected ranks were computed with (taken by the
+                          first dfpr_apply_batch after the ranks were computed
+                          or set), every vertex is recomputed from then on.
+                          This is a reading; the paper's runs use self-loops
+                          (Sec. 5.1.3). */
 };
 
 /* Schedules of the rank iteration. */

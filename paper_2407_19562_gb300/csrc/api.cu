@@ -150,9 +150,8 @@ dfpr_status run_update(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, Run
   DFPR_REQUIRE(!(p.normalize && g->nparts > 1), DFPR_EINVAL,
                "normalize is not supported for a set of graphs");
   if (g->cfg.dead_end == DFPR_TELEPORT)
-    DFPR_REQUIRE(kind != kRunDF && p.mode == DFPR_MODE_JACOBI, DFPR_EINVAL,
-                 "teleport dead-end handling is supported by the jacobi static / naive-dynamic "
-                 "schedules only");
+    DFPR_REQUIRE(p.mode == DFPR_MODE_JACOBI, DFPR_EINVAL,
+                 "teleport dead-end handling is supported by the jacobi schedule only");
   dfpr_stats local;
   memset(&local, 0, sizeof local);
   local.rank_sum = NAN;
@@ -161,6 +160,7 @@ dfpr_status run_update(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, Run
     return DFPR_OK;
   }
   dfpr_status r = run_iteration(g, p, kind, &local);
+  g->d_before_valid = false;  // the ranks were recomputed
   if (p.normalize && r == DFPR_OK) local.rank_sum = rank_sum(g);
   if (st) *st = local;
   if (r != DFPR_OK)
@@ -427,6 +427,10 @@ dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_sr
   const int32_t* is = stage_in(g, c, ins_src, n_ins, on_device);
   const int32_t* id = stage_in(g, d, ins_dst, n_ins, on_device);
   long long applied[2] = {0, 0};
+  if (g->cfg.dead_end == DFPR_TELEPORT && !g->d_before_valid) {
+    g->d_before = dangling_mass(g);  // the D the current ranks were computed with
+    g->d_before_valid = true;
+  }
   graph_apply(g, ds, dd, n_del, is, id, n_ins, applied);
   DFPR_CUDA(cudaStreamSynchronize(g->stream));
   if (n_applied) {
@@ -533,6 +537,7 @@ dfpr_status dfpr_set_ranks(dfpr_graph* g, const double* ranks, int on_device) {
     DFPR_LAUNCHED();
   }
   refresh_contributions(g);
+  g->d_before_valid = false;  // new ranks: their dead-end mass is taken at the next batch
   DFPR_CUDA(cudaStreamSynchronize(s));
   return DFPR_OK;
   API_END

@@ -206,6 +206,11 @@ struct dfpr_graph {
   int bits = 1;             // ids fit in `bits` bits
   long long m = 0;          // live edges (both directions hold m)
   long long last_real_del = 0;  // real deletions of the batch being applied
+  // teleport graphs: dead-end mass of the ranks before the first batch applied
+  // since the ranks were last computed or set (the D those ranks were
+  // computed with); d_before_valid is false when no batch is pending
+  double d_before = 0.0;
+  bool d_before_valid = false;
   dfpr_graph_config cfg;
   dfpr::Rows out, in;
   // ranks: FP64 or FP32 arrays (one of each pair is used)

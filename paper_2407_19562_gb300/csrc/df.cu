@@ -1930,6 +1930,15 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
   }
   const int grid = persistent_grid(g, p, (const void*)k_jacobi<P>);
   const unsigned long long fault_seed0 = a.fault_seed;
+  // DF with teleport dead ends: every rank holds alpha * D / n, D the dead-end
+  // mass. Ranks outside the affected set were computed with D_last; once the
+  // current D differs from it by more than tol_f * n / alpha (relative to the
+  // mean rank 1/n in FP32 mode), every vertex is recomputed from then on.
+  // D_last starts at the mass the ranks had before the batch.
+  const bool tdf = df && a.teleport;
+  const double D_last = g->d_before_valid ? g->d_before : NAN;
+  const double shift_tol = P::relative ? a.tol_f / (double)g->n : a.tol_f;
+  bool all = false;
   int it = 0;
   double last = 0.0;
   bool converged = false;
@@ -1940,9 +1949,16 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
       k_dangling<V><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, a.R, &g->ctl.p->dsum);
       DFPR_LAUNCHED();
     }
+    if (tdf && !all) {
+      const unsigned long long bits = read_word(g, &g->ctl.p->dsum, sizeof(double));
+      double D;
+      memcpy(&D, &bits, sizeof D);
+      if (!(p.alpha * std::fabs(D - D_last) / (double)g->n <= shift_tol)) all = true;  // NaN: unknown
+    }
+    const bool listed = df && !all;
     a.fault_seed = host_mix64(fault_seed0 + (unsigned long long)it);  // fresh delay draws per iteration
-    k_jacobi<P><<<grid, kNT, 0, s>>>(a, a.R, a.C, R2, C2, df ? g->affected_list.p : nullptr, count,
-                                     df ? 1 : 0);
+    k_jacobi<P><<<grid, kNT, 0, s>>>(a, a.R, a.C, R2, C2, listed ? g->affected_list.p : nullptr,
+                                     listed ? count : (long long)g->n, listed ? 1 : 0);
     DFPR_LAUNCHED();
     DFPR_CUDA(cudaMemcpyAsync(g->pinned, &g->ctl.p->max_change_bits, sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, s));
@@ -1950,7 +1966,7 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
                               cudaMemcpyDeviceToHost, s));
     DFPR_CUDA(cudaStreamSynchronize(s));
     memcpy(&last, &g->pinned[0], sizeof last);
-    if (df) count = (long long)g->pinned[1];
+    if (df && !all) count = (long long)g->pinned[1];
     // swap R <-> R2, C <-> C2
     swap_vectors<P>(g);
     std::swap(R2, a.R);
@@ -1967,7 +1983,7 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
     fill_stats(h.c, st);
     st->passes = it;
     st->residual_linf = last;
-    st->affected = df ? count : g->n;
+    st->affected = df && !all ? count : g->n;
   }
   if (df) {
     k_clear_list<<<grid_small(count), kNT, 0, s>>>(g->affected_list.p, count, g->va_bits.p, nullptr);
@@ -2103,6 +2119,21 @@ double rank_sum(dfpr_graph* g) {
     k_sum_ranks<double><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->R64.p, sum);
   else
     k_sum_ranks<float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->R32.p, sum);
+  DFPR_LAUNCHED();
+  unsigned long long bits = read_word(g, sum, sizeof(double));
+  double d;
+  memcpy(&d, &bits, sizeof d);
+  return d;
+}
+
+double dangling_mass(dfpr_graph* g) {
+  cudaStream_t s = g->stream;
+  double* sum = (double*)(g->host_sync.p + 8);
+  DFPR_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), s));
+  if (g->cfg.precision == DFPR_FP64)
+    k_dangling<double><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, sum);
+  else
+    k_dangling<float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, sum);
   DFPR_LAUNCHED();
   unsigned long long bits = read_word(g, sum, sizeof(double));
   double d;

@@ -27,4 +27,7 @@ void reset_ranks(dfpr_graph* g);
 // FP64 sum of the ranks.
 double rank_sum(dfpr_graph* g);
 
+// FP64 sum of the ranks of dead ends (vertices without out-edges).
+double dangling_mass(dfpr_graph* g);
+
 }  // namespace dfpr

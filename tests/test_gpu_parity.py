@@ -309,7 +309,7 @@ def test_teleport_static_matches_reference(gpu_lib):
     assert st.status == gpu_lib.OK
     ref, _ = oracle.Graph.build(n, src, dst, False).reference(dead_end=1)
     assert np.max(np.abs(g.get_ranks() - ref)) <= LINF64
-    # the frontier schedules need self-loops (no global dead-end term)
+    # the worklist and round schedules need self-loops (no global dead-end term)
     with pytest.raises(gpu_lib.DfprError):
         g.df_pagerank()
     with pytest.raises(gpu_lib.DfprError):
