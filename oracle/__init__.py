@@ -248,10 +248,12 @@ class Graph:
         return R, _stats(st)
 
 
-def sample_rows(n, src, dst, which, direction="out", self_loops=True, batch=None):
+def sample_rows(n, src, dst, which, direction="out", self_loops=True, batch=None, cap=1 << 16):
     """Rows of G^1 = apply(build(src, dst), batch) for the vertices in `which`
     (distinct), computed straight from the raw edges. batch is
-    (del_src, del_dst, ins_src, ins_dst) or None. Returns a list of int32 arrays."""
+    (del_src, del_dst, ins_src, ins_dst) or None. cap: first guess of the
+    total row length (grown and retried when short). Returns a list of int32
+    arrays."""
     lib = _load()
     src, dst = _i32(src), _i32(dst)
     which = _i32(which)
@@ -259,7 +261,6 @@ def sample_rows(n, src, dst, which, direction="out", self_loops=True, batch=None
         e = np.zeros(0, np.int32)
         batch = (e, e, e, e)
     ds, dd, is_, id_ = map(_i32, batch)
-    cap = 1 << 16
     while True:
         off = np.zeros(len(which) + 1, np.int64)
         idx = np.empty(cap, np.int32)

@@ -108,6 +108,19 @@ struct Scratch {
 
 // One row of CSR or CSC: edges[off .. off + deg) hold the row, sorted; the
 // slot reserves cap >= deg entries so that batches update it in place.
+// Per-vertex worklist record: X = the rank at the vertex's last expansion,
+// ep = the epoch (call) in which X was written; X is meaningful only when
+// ep is the current call's epoch.
+struct __align__(16) XE64 {
+  double x;
+  uint32_t ep;
+  uint32_t pad;
+};
+struct __align__(8) XE32 {
+  float x;
+  uint32_t ep;
+};
+
 struct __align__(16) RowDesc {
   long long off;
   int deg;
@@ -214,14 +227,17 @@ struct dfpr_graph {
   dfpr_graph_config cfg;
   dfpr::Rows out, in;
   // ranks: FP64 or FP32 arrays (one of each pair is used)
-  dfpr::DevArray<double> R64, X64;         // rank, rank at last expansion
+  dfpr::DevArray<double> R64;              // rank
   dfpr::DevArray<long long> C64;           // contribution R/outdeg, fixed point 2^-62
-  dfpr::DevArray<float> R32, C32, X32;
+  dfpr::DevArray<float> R32, C32;
+  // worklist: rank at the last expansion and the epoch (call) that wrote it,
+  // one record per vertex so that both come in one load
+  dfpr::DevArray<dfpr::XE64> XE64;
+  dfpr::DevArray<dfpr::XE32> XE32;
   dfpr::DevArray<double> R64b;             // second vectors of the Jacobi schedule
   dfpr::DevArray<long long> C64b;
   dfpr::DevArray<float> R32b, C32b;
-  dfpr::DevArray<uint32_t> ep;            // epoch of first recomputation in the current call
-  uint32_t epoch = 0;
+  uint32_t epoch = 0;                     // the current call's epoch
   dfpr::DevArray<uint32_t> state;         // 2 bits per vertex: bit0 queued, bit1 running
   dfpr::DevArray<int32_t> queue;          // qcap slots, -1 when empty
   unsigned long long qcap = 0;

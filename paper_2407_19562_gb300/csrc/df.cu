@@ -103,6 +103,18 @@ struct P64 {
   static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
   static __device__ __forceinline__ contrib load_c(const contrib* p) { return __ldcg(p); }
   static __device__ __forceinline__ acc shfl_xor(acc a, int d) { return __shfl_xor_sync(kFull, a, d); }
+  using xe = XE64;
+  static __device__ __forceinline__ void load_xe(const xe* p, val& x, uint32_t& ep) {
+    const longlong2 b = __ldcg(reinterpret_cast<const longlong2*>(p));
+    x = __longlong_as_double(b.x);
+    ep = (uint32_t)(b.y & 0xffffffffll);
+  }
+  static __device__ __forceinline__ void store_xe(xe* p, val x, uint32_t ep) {
+    longlong2 b;
+    b.x = __double_as_longlong(x);
+    b.y = (long long)ep;
+    *reinterpret_cast<longlong2*>(p) = b;
+  }
   // heavy-gather jobs: partial sums meet in one 64-bit word (exact integer adds)
   static __device__ __forceinline__ void job_add(unsigned long long* p, acc x) {
     atomicAdd(p, (unsigned long long)x);
@@ -136,6 +148,15 @@ struct P32 {
   }
   static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
   static __device__ __forceinline__ contrib load_c(const contrib* p) { return __ldcg(p); }
+  using xe = XE32;
+  static __device__ __forceinline__ void load_xe(const xe* p, val& x, uint32_t& ep) {
+    const uint2 b = __ldcg(reinterpret_cast<const uint2*>(p));
+    x = __uint_as_float(b.x);
+    ep = b.y;
+  }
+  static __device__ __forceinline__ void store_xe(xe* p, val x, uint32_t ep) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(__float_as_uint(x), ep);
+  }
   static __device__ __forceinline__ acc shfl_xor(acc a, int d) {
     return {__shfl_xor_sync(kFull, a.s, d), __shfl_xor_sync(kFull, a.c, d)};
   }
@@ -173,8 +194,7 @@ struct Args {
   const int32_t* __restrict__ out_edges;
   typename P::val* R;
   typename P::contrib* C;
-  typename P::val* X;
-  uint32_t* ep;
+  typename P::xe* XE;
   uint32_t epoch;
   uint32_t* state;
   int32_t* queue;
@@ -757,6 +777,8 @@ __device__ __forceinline__ void note_done(const Args<P>& a, int v, int lane) {
 // Worklist schedule
 // ---------------------------------------------------------------------------
 
+constexpr double kDriftFactor = 10.0;
+
 // Eq. 1 epilogue of one recomputed vertex v (lane-local): new rank r from the
 // gathered sum; Delta r against the stored rank; the rank at the last
 // expansion decides whether v marks its out-neighbours; the state's queued
@@ -770,21 +792,21 @@ __device__ __forceinline__ void vertex_epilogue(const Args<P>& a, int v, double 
   double s2 = sum;
   if (a.teleport) s2 += dangling / (double)a.n;
   const typename P::val r = (typename P::val)(base_of(a, v) + a.alpha * s2);
-  typename P::val x0;
   fresh = e_tag != a.epoch;
-  if (fresh) {
-    a.ep[v] = a.epoch;
-    x0 = r_old;
-  } else {
-    x0 = x_prev;
-  }
+  const typename P::val x0 = fresh ? r_old : x_prev;
   const double dr = fabs((double)r - (double)r_old);
   a.R[v] = r;
   a.C[v] = contrib_of(r, od);
   const double thr_f = frontier_thr<P>(a.tol_f, r);
   const double thr = P::relative ? a.tol * fabs((double)r) : a.tol;
-  expand = fabs((double)r - (double)x0) > thr_f;
-  a.X[v] = expand ? r : x0;
+  // FP64: the paper's rule (this recomputation moved r by more than tau_f),
+  // plus a bound on what dependants can miss without Alg. 2's repeated
+  // passes: also expand once r has drifted by more than kDriftFactor * tau_f
+  // since the last expansion. FP32: the drift rule alone (its relative
+  // tolerance needs every sub-threshold change accounted for).
+  const double drift = fabs((double)r - (double)x0);
+  expand = P::relative ? drift > thr_f : (dr > thr_f || drift > kDriftFactor * thr_f);
+  P::store_xe(a.XE + v, expand ? r : x0, a.epoch);
   requeue = dr > thr;
   st.max_change = fmax(st.max_change, dr);
 }
@@ -858,8 +880,9 @@ __device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk,
   if (vv >= 0) {
     const double sum = P::job_total(ld_volatile(a.job_sum + slot));
     const typename P::val r_old = P::load(a.R + vv);
-    const uint32_t e_tag = __ldcg(a.ep + vv);
-    const typename P::val x_prev = P::load(a.X + vv);
+    uint32_t e_tag;
+    typename P::val x_prev;
+    P::load_xe(a.XE + vv, x_prev, e_tag);
     orow = load_row(a.out_rows + vv);
     const double dangling = a.teleport ? a.ctl->dsum : 0.0;
     vertex_epilogue(a, vv, sum, r_old, e_tag, x_prev, orow.deg, dangling, expand, requeue, fresh,
@@ -1067,8 +1090,7 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     orow.deg = 0;
     if (v >= 0) {
       r_old = P::load(a.R + v);
-      e_tag = __ldcg(a.ep + v);
-      x_prev = P::load(a.X + v);
+      P::load_xe(a.XE + v, x_prev, e_tag);
       orow = load_row(a.out_rows + v);
     }
     const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
@@ -1605,7 +1627,6 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   a.in_edges = g->in.edges.p;
   a.out_rows = g->out.rows.p;
   a.out_edges = g->out.edges.p;
-  a.ep = g->ep.p;
   a.epoch = g->epoch;
   a.state = g->state.p;
   a.queue = g->queue.p;
@@ -1665,13 +1686,13 @@ template <>
 void set_vectors<P64>(dfpr_graph* g, Args<P64>& a) {
   a.R = g->R64.p;
   a.C = g->C64.p;
-  a.X = g->X64.p;
+  a.XE = g->XE64.p;
 }
 template <>
 void set_vectors<P32>(dfpr_graph* g, Args<P32>& a) {
   a.R = g->R32.p;
   a.C = g->C32.p;
-  a.X = g->X32.p;
+  a.XE = g->XE32.p;
 }
 
 int persistent_grid(dfpr_graph* g, const dfpr_params& p, const void* kernel) {
@@ -2034,7 +2055,10 @@ dfpr_status run_any(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stat
   if (kind == kRunStatic) reset_ranks(g);
   g->epoch += 1;
   if (g->epoch == 0) {  // wrapped: clear epochs so that no vertex looks current
-    DFPR_CUDA(cudaMemsetAsync(g->ep.p, 0, sizeof(uint32_t) * g->n, s));
+    if (g->cfg.precision == DFPR_FP64)
+      DFPR_CUDA(cudaMemsetAsync(g->XE64.p, 0, sizeof(XE64) * g->n, s));
+    else
+      DFPR_CUDA(cudaMemsetAsync(g->XE32.p, 0, sizeof(XE32) * g->n, s));
     g->epoch = 1;
   }
   dfpr_status r;
@@ -2063,14 +2087,14 @@ void alloc_iteration_state(dfpr_graph* g) {
   if (g->cfg.precision == DFPR_FP64) {
     g->R64.reset(n, s);
     g->C64.reset(n, s);
-    g->X64.reset(n, s);
+    g->XE64.reset(n, s);
+    DFPR_CUDA(cudaMemsetAsync(g->XE64.p, 0, sizeof(XE64) * n, s));
   } else {
     g->R32.reset(n, s);
     g->C32.reset(n, s);
-    g->X32.reset(n, s);
+    g->XE32.reset(n, s);
+    DFPR_CUDA(cudaMemsetAsync(g->XE32.p, 0, sizeof(XE32) * n, s));
   }
-  g->ep.reset(n, s);
-  DFPR_CUDA(cudaMemsetAsync(g->ep.p, 0, sizeof(uint32_t) * n, s));
   g->epoch = 0;
   g->state.reset(((size_t)n + 15) / 16, s);
   DFPR_CUDA(cudaMemsetAsync(g->state.p, 0, sizeof(uint32_t) * g->state.count, s));

@@ -1,0 +1,84 @@
+"""Parity at the benchmark's full size: R-MAT scale 24 (16.8M vertices, 280M
+edges with self-loops), one batch of 1e-4 |E|, FP64, worklist schedule, the
+default launch configuration the benchmark times.
+
+The oracle cannot build this graph or compute its reference ranks in a test's
+time, so it checks what it can compute one vertex at a time, straight from
+the raw edges and the batch (oracle.sample_rows):
+
+- the CSR and CSC rows of sampled vertices, bit for bit;
+- Eq. 1 at sampled vertices. When the update ends, a vertex v was last
+  recomputed from its in-neighbours' ranks, and none of them expanded
+  afterwards. A vertex that does not expand has drifted by at most
+  DRIFT * tau_f from its rank at its last expansion, so each in-neighbour
+  moved by at most 2 DRIFT tau_f since v read it: the residual |r(v) - R[v]|
+  of Eq. 1 evaluated on the final ranks is at most
+  alpha * 2 DRIFT tau_f * sum_u 1/|out(u)|, plus the residual R^0 had (a
+  vertex the update never recomputed keeps it), plus rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+ALPHA = 0.85
+TOL = 1e-10
+TOL_F = TOL / 1000
+DRIFT = 10.0  # drift since the last expansion that forces one (worklist schedule)
+
+
+@pytest.fixture(scope="module")
+def full():
+    n, src, dst = workloads.rmat_graph(24, 16, 3)
+    b = 28021  # 1e-4 of the 280,209,127 edges with self-loops
+    batch = workloads.uniform_batch(n, b, 100, src, dst)
+    rng = np.random.default_rng(77)
+    hubs = np.argsort(np.bincount(dst, minlength=n))[-4:]
+    # rows checked bit for bit: random vertices, the largest in-rows, batch endpoints
+    sample = np.unique(np.concatenate([rng.integers(0, n, 1500), hubs,
+                                       batch[0][:50], batch[2][:50]])).astype(np.int32)
+    # Eq. 1 checked at random vertices and at targets of inserted edges (uniform,
+    # so their in-neighbours' out-rows stay small enough to rebuild)
+    resid = np.unique(np.concatenate([rng.integers(0, n, 300), batch[3][:20]])).astype(np.int32)
+    return dict(n=n, src=src, dst=dst, batch=batch, sample=sample, resid=resid)
+
+
+def test_full_size_rows_and_eq1_residual(gpu_lib, full):
+    n, src, dst, batch, sample = full["n"], full["src"], full["dst"], full["batch"], full["sample"]
+    g = gpu_lib.graph_load(n, src, dst)
+    assert g.info()["m"] == 280209127
+    st0 = g.static_pagerank(gpu_lib.default_params(mode=gpu_lib.JACOBI, tol=TOL / 1000, max_iter=1000))
+    assert st0.status == gpu_lib.OK
+    g.apply_batch(*batch)
+    st = g.df_pagerank(gpu_lib.default_params())
+    assert st.status == gpu_lib.OK
+    R = g.get_ranks()
+
+    # rows of the updated graph, bit for bit
+    out_rows = oracle.sample_rows(n, src, dst, sample, "out", batch=batch)
+    in_rows = oracle.sample_rows(n, src, dst, sample, "in", batch=batch)
+    off, idx = g.get_csr()
+    for v, row in zip(sample, out_rows):
+        assert np.array_equal(idx[off[v]:off[v + 1]], row), v
+    coff, cidx = g.get_csc()
+    for v, row in zip(sample, in_rows):
+        assert np.array_equal(cidx[coff[v]:coff[v + 1]], row), v
+    del off, idx, coff, cidx
+
+    # Eq. 1 on the final ranks, with rows and out-degrees from the oracle
+    resid = full["resid"]
+    rin = oracle.sample_rows(n, src, dst, resid, "in", batch=batch)
+    nbrs = np.unique(np.concatenate(rin)).astype(np.int32)
+    nbr_deg = np.array([len(r) for r in oracle.sample_rows(n, src, dst, nbrs, "out", batch=batch,
+                                                           cap=1 << 26)], np.float64)
+    for v, row in zip(resid, rin):
+        d = nbr_deg[np.searchsorted(nbrs, row)]
+        r = (1.0 - ALPHA) / n + ALPHA * float(np.sum(R[row] / d))
+        # R^0 (static, iterate difference <= tol / 1000) is where vertices the
+        # update did not recompute keep their rank: allow its residual too
+        bound = ALPHA * 2.0 * DRIFT * TOL_F * float(np.sum(1.0 / d)) + TOL / 1000 + 1e-14
+        assert abs(r - R[v]) <= bound, (int(v), abs(r - R[v]), bound)
+    assert np.all(R > 0)
