@@ -140,7 +140,7 @@ typedef struct dfpr_params {
 typedef struct dfpr_stats {
   int64_t processed;      /* vertex rank recomputations */
   int64_t edges_gathered; /* in-edges read by those recomputations */
-  int64_t expansions;     /* recomputations whose change exceeded tau_f */
+  int64_t expansions;     /* recomputations that marked their out-neighbours */
   int64_t edges_marked;   /* out-edges visited by marking and expansion */
   int64_t pushes;         /* work-queue insertions (worklist mode) */
   int64_t affected;       /* distinct vertices recomputed at least once */
@@ -233,7 +233,11 @@ dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_sr
  * DFPR_MODE_ROUND, the work-queue schedule for DFPR_MODE_WORKLIST): starting
  * from the current ranks R^{t-1}, marks the affected vertices of the pending
  * change set and iterates Eq. 1 over them until convergence, in place. Clears
- * the pending change set. With no pending changes it returns at once with 0
+ * the pending change set. A recomputed vertex marks its out-neighbours when
+ * its rank moved by more than tau_f (Alg. 1, Alg. 2). The worklist schedule
+ * recomputes only marked vertices, so there a vertex also marks them once its
+ * rank has drifted by more than 10 tau_f since it last did (in FP32 mode:
+ * by more than tau_f, the only rule), which bounds what a dependant misses. With no pending changes it returns at once with 0
  * recomputations. p NULL selects the defaults; stats may be NULL.
  * Returns ENOTCONV / ETIMEOUT when the cap / budget stopped the iteration
  * (ranks are then valid but not converged), EINVAL for bad parameters.
