@@ -158,6 +158,7 @@ struct DfCtl {
   HotU64 thead;       // token ring (chunks of heavy gathers and of marking): consumers
   HotU64 ttail;       //   producers
   HotI64 tavail;      //   published, not yet claimed
+  HotI64 open_tokens; // round: gather tokens published and not yet summed
   HotU64 fhead;       // free ring of heavy-gather job slots: consumers
   HotU64 ftail;       //   producers
   HotI64 favail;      //   free slots

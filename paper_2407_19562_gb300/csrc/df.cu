@@ -388,15 +388,8 @@ __device__ __forceinline__ void load_chunk_ids(const int32_t* __restrict__ edges
 // memory round trip, not two. Each chunk is reduced by a segmented warp scan
 // whose segment tails add into s_acc[owner].
 template <class P>
-__device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl, long long* s_off,
-                                  typename P::acc* s_acc, WarpStats& st) {
-  int deg = 0;
-  long long off = 0;
-  if (v >= 0) {
-    const RowDesc r = load_row(a.in_rows + v);
-    deg = r.deg;
-    off = r.off;
-  }
+__device__ typename P::acc gather_row(const Args<P>& a, int deg, long long off, int lane, int* s_excl,
+                                      long long* s_off, typename P::acc* s_acc, WarpStats& st) {
   int incl = deg;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -441,6 +434,18 @@ __device__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl
   }
   if (lane == 0) st.c[kStEdges] += (unsigned long long)total;
   return s_acc[lane];
+}
+
+// gather_row over the in-row of v (nothing when v < 0).
+template <class P>
+__device__ __forceinline__ typename P::acc gather(const Args<P>& a, int v, int lane, int* s_excl,
+                                                  long long* s_off, typename P::acc* s_acc,
+                                                  WarpStats& st) {
+  RowDesc r;
+  r.off = 0;
+  r.deg = 0;
+  if (v >= 0) r = load_row(a.in_rows + v);
+  return gather_row(a, r.deg, r.off, lane, s_excl, s_off, s_acc, st);
 }
 
 // Per-warp buffer of queue insertions in shared memory, flushed to the ring
@@ -564,7 +569,7 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
 // `pending` grows first, so the iteration cannot end while they are outstanding.
 template <class P>
 __device__ void push_tokens(const Args<P>& a, int cnt, unsigned kind, unsigned x, int lane,
-                            WarpStats& st) {
+                            WarpStats& st, long long* open) {
   int incl = cnt;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -575,7 +580,7 @@ __device__ void push_tokens(const Args<P>& a, int cnt, unsigned kind, unsigned x
   if (total == 0) return;
   unsigned long long base = 0;
   if (lane == 0) {
-    atomic_add_ll(&a.ctl->pending.v, total);
+    atomic_add_ll(open, total);
     fence_acq_rel();
     base = atomicAdd(&a.ctl->ttail.v, (unsigned long long)total);
   }
@@ -670,7 +675,8 @@ template <class P>
 __device__ void expand_rows(const Args<P>& a, int v, int od, long long oo, int lane, int* s_excl,
                             long long* s_off, PushBuf pb, WarpStats& st) {
   const bool split = od > kMarkSplit;
-  push_tokens(a, split ? (od + kMarkSplit - 1) / kMarkSplit : 0, 1u, (unsigned)max(v, 0), lane, st);
+  push_tokens(a, split ? (od + kMarkSplit - 1) / kMarkSplit : 0, 1u, (unsigned)max(v, 0), lane, st,
+              &a.ctl->pending.v);
   if (split) od = 0;
   int incl = od;
 #pragma unroll
@@ -841,9 +847,12 @@ __device__ int finish_vertices(const Args<P>& a, int v, bool expand, bool requeu
 
 // Gather token: sums one chunk of a heavy vertex's in-row into its job; the
 // warp that sums the last chunk finishes the vertex.
+// Sums chunk `chunk` of the in-row of job `slot`'s vertex into the job
+// (exact integer adds in FP64 mode). Returns, warp-uniform, whether this warp
+// summed the last chunk; *vout receives the vertex.
 template <class P>
-__device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk, int lane,
-                                int* s_excl, long long* s_off, PushBuf pb, WarpStats& st) {
+__device__ bool sum_gather_token(const Args<P>& a, unsigned slot, unsigned chunk, int lane,
+                                 WarpStats& st, int* vout) {
   fence_acq_rel();  // the job record was published before the token
   const int v = ld_volatile(a.job_v + slot);
   const RowDesc row = load_row(a.in_rows + v);
@@ -872,8 +881,15 @@ __device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk,
     last = atomicSub(a.job_rem + slot, 1) == 1;
     st.c[kStEdges] += (unsigned long long)max(0ll, end - beg);
   }
-  last = __shfl_sync(kFull, last, 0);
-  if (!last) return 0;
+  *vout = v;
+  return __shfl_sync(kFull, last, 0) != 0;
+}
+
+template <class P>
+__device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk, int lane,
+                                int* s_excl, long long* s_off, PushBuf pb, WarpStats& st) {
+  int v = -1;
+  if (!sum_gather_token(a, slot, chunk, lane, st, &v)) return 0;
   // finish the heavy vertex (lane 0 owns it)
   fence_acq_rel();
   const int vv = lane == 0 ? v : -1;
@@ -1079,7 +1095,7 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       }
       const unsigned jobs_b = __ballot_sync(kFull, nch > 0);
       if (jobs_b) {
-        push_tokens(a, nch, 0u, (unsigned)max(slot, 0), lane, st);
+        push_tokens(a, nch, 0u, (unsigned)max(slot, 0), lane, st, &ctl->pending.v);
         if (lane == 0) sc[kStJobs] += (unsigned long long)__popc(jobs_b);
         if (nch > 0) v = -1;
       }
@@ -1162,6 +1178,100 @@ __device__ void mark_round(const Args<P>& a, int t, bool valid, int lane) {
   if (fresh) *(volatile int*)(a.alist + base + __popc(b & lanemask_lt())) = t;
 }
 
+// Alg. 2 epilogue for each lane's vertex v (or -1), from sum = the sum of its
+// in-neighbours' contributions: writes R and C; when the change exceeds
+// tau_f, marks the out-neighbours affected and not converged (with
+// self-loops this flags v itself); when it is at most tau, clears v's R_C
+// flag; then ends v's exclusion. Warp-uniform. Returns whether this lane
+// cleared a flag.
+template <class P>
+__device__ bool round_finish(const Args<P>& a, int v, double sum, int lane, int* s_excl,
+                             long long* s_off, WarpStats& st) {
+  bool expand = false;
+  double dr = 0.0, thr = 0.0;
+  if (v >= 0) {
+    const typename P::val r = (typename P::val)(base_of(a, v) + a.alpha * sum);
+    const typename P::val r_old = P::load(a.R + v);
+    dr = fabs((double)r - (double)r_old);
+    const int od = a.out_rows[v].deg;
+    a.R[v] = r;
+    a.C[v] = contrib_of(r, od);
+    const double thr_f = frontier_thr<P>(a.tol_f, r);
+    thr = P::relative ? a.tol * fabs((double)r) : a.tol;
+    expand = dr > thr_f;
+    st.max_change = fmax(st.max_change, dr);
+  }
+  stats_count(st, kStExpansions, expand, lane);
+  // expansion first (with self-loops it flags v itself), then v's own flag
+  {
+    int od = 0;
+    long long oo = 0;
+    if (expand) {
+      const RowDesc r = a.out_rows[v];
+      od = r.deg;
+      oo = r.off;
+    }
+    int incl = od;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    s_excl[lane] = incl - od;
+    s_off[lane] = oo;
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+      const int e = base + lane;
+      const bool valid = e < total;
+      int t = 0;
+      if (valid) {
+        const int o = owner_of(s_excl, e);
+        t = a.out_edges[s_off[o] + (e - s_excl[o])];
+      }
+      mark_round(a, t, valid, lane);
+    }
+    if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
+  }
+  bool conv = false;
+  if (v >= 0 && dr <= thr) {
+    const uint32_t bit = 1u << (v & 31);
+    conv = (atomicAnd(a.rc_bits + (v >> 5), ~bit) & bit) != 0u;
+  }
+  if (v >= 0) {
+    __threadfence();
+    const unsigned sh = (unsigned)(v & 15) * 2u;
+    atomicAnd(a.state + (v >> 4), ~(2u << sh));
+  }
+  return conv;
+}
+
+// Round schedule: a gather token (a chunk of a heavy vertex's in-row); the
+// warp that sums the last chunk finishes the vertex with round_finish.
+template <class P>
+__device__ void round_gather_token(const Args<P>& a, unsigned slot, unsigned chunk, int lane,
+                                   int* s_excl, long long* s_off, WarpStats& st) {
+  int v = -1;
+  if (sum_gather_token(a, slot, chunk, lane, st, &v)) {
+    fence_acq_rel();
+    double sum = 0.0;
+    if (lane == 0) sum = P::job_total(ld_volatile(a.job_sum + slot));
+    const bool conv = round_finish(a, lane == 0 ? v : -1, sum, lane, s_excl, s_off, st);
+    if (lane == 0) {
+      free_job(a, (int)slot);
+      if (conv) atomic_add_ll(&a.ctl->nc.v, -1);
+      atomicAdd(&a.ctl->processed.v, 1ull);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence();  // the chunk's sum (and a finished vertex) before the count drops
+    atomic_add_ll(&a.ctl->open_tokens.v, -1);
+  }
+  __syncwarp();
+}
+
 template <class P>
 __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
   __shared__ int s_excl[kWPB][32];
@@ -1225,6 +1335,14 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
   unsigned long long fk = 0;  // chunks this warp has taken (fault simulation)
   for (; pass < a.max_iter; ++pass) {
     while (true) {
+      {  // chunks of heavy gathers first: they finish vertices other warps wait on
+        const unsigned long long tok = pop_token(a, lane);
+        if (tok != kNoToken) {
+          round_gather_token(a, (unsigned)((tok >> 31) & 0x7fffffffull),
+                             (unsigned)(tok & 0x7fffffffull), lane, s_excl[w], s_off[w], st);
+          continue;
+        }
+      }
       unsigned long long c = 0;
       long long len = 0;
       if (lane == 0) {
@@ -1259,88 +1377,80 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
         if (atomicOr(a.state + (v >> 4), 2u << sh) & (2u << sh)) v = -1;
       }
       __threadfence();
-      const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
-      bool expand = false;
-      double dr = 0.0, thr = 0.0;
-      if (v >= 0) {
-        const typename P::val r = finish_rank(a, acc, 0.0, v);
-        const typename P::val r_old = P::load(a.R + v);
-        dr = fabs((double)r - (double)r_old);
-        const int od = a.out_rows[v].deg;
-        a.R[v] = r;
-        a.C[v] = contrib_of(r, od);
-        const double thr_f = frontier_thr<P>(a.tol_f, r);
-        thr = P::relative ? a.tol * fabs((double)r) : a.tol;
-        expand = dr > thr_f;
-        st.max_change = fmax(st.max_change, dr);
-      }
-      stats_count(st, kStExpansions, expand, lane);
-      // expansion first (with self-loops it flags v itself), then v's own flag
+      RowDesc irow;
+      irow.off = 0;
+      irow.deg = 0;
+      if (v >= 0) irow = load_row(a.in_rows + v);
+      // Heavy in-rows become jobs of gather tokens that any warp can take
+      // (taken before new chunks); the vertex stays excluded until the warp
+      // that sums its last chunk finishes it.
       {
-        int od = 0;
-        long long oo = 0;
-        if (expand) {
-          const RowDesc r = a.out_rows[v];
-          od = r.deg;
-          oo = r.off;
-        }
-        int incl = od;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          int y = __shfl_up_sync(kFull, incl, d);
-          if (lane >= d) incl += y;
-        }
-        const int total = __shfl_sync(kFull, incl, 31);
-        __syncwarp();
-        s_excl[w][lane] = incl - od;
-        s_off[w][lane] = oo;
-        __syncwarp();
-        for (int base = 0; base < total; base += 32) {
-          const int e = base + lane;
-          const bool valid = e < total;
-          int t = 0;
-          if (valid) {
-            int lo = 0, hi = 32;
-            while (hi - lo > 1) {
-              const int mid = (lo + hi) >> 1;
-              if (s_excl[w][mid] <= e) lo = mid; else hi = mid;
-            }
-            t = a.out_edges[s_off[w][lo] + (e - s_excl[w][lo])];
+        int nch = 0, slot = -1;
+        if (v >= 0 && irow.deg > kGatherChunk) {
+          slot = alloc_job(a);
+          if (slot >= 0) {
+            nch = (irow.deg + kGatherChunk - 1) / kGatherChunk;
+            a.job_v[slot] = v;
+            a.job_sum[slot] = 0ull;
+            a.job_rem[slot] = nch;
+            fence_acq_rel();
           }
-          mark_round(a, t, valid, lane);
         }
-        if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
-      }
-      long long conv = 0;
-      if (v >= 0) {
-        if (dr <= thr) {
-          const uint32_t bit = 1u << (v & 31);
-          if (atomicAnd(a.rc_bits + (v >> 5), ~bit) & bit) conv = 1;
+        if (__ballot_sync(kFull, nch > 0)) {
+          push_tokens(a, nch, 0u, (unsigned)max(slot, 0), lane, st, &ctl->open_tokens.v);
+          if (nch > 0) {
+            v = -1;
+            irow.deg = 0;
+          }
         }
       }
-      if (v >= 0) {
-        __threadfence();
-        const unsigned sh = (unsigned)(v & 15) * 2u;
-        atomicAnd(a.state + (v >> 4), ~(2u << sh));
-      }
+      const typename P::acc acc = gather_row(a, irow.deg, irow.off, lane, s_excl[w], s_off[w],
+                                             s_acc[w], st);
+      const long long conv = round_finish(a, v, P::total(acc), lane, s_excl[w], s_off[w], st) ? 1 : 0;
       const unsigned cb = __ballot_sync(kFull, conv != 0);
+      const unsigned pb_ = __ballot_sync(kFull, v >= 0);
       if (lane == 0) {
         if (cb) atomic_add_ll(&ctl->nc.v, -(long long)__popc(cb));
-        const int cnt = (int)min(32ll, len - (long long)c);
-        atomicAdd(&ctl->processed.v, (unsigned long long)cnt);
+        atomicAdd(&ctl->processed.v, (unsigned long long)__popc(pb_));
       }
       fault_delay(a, fk, v >= 0, lane);
       ++fk;
     }
-    int stop = 0;
-    if (lane == 0) {
-      if (ld_volatile(&ctl->nc.v) <= 0 || ld_volatile(&ctl->abort)) stop = 1;
-      else if (timed_out(a)) {
-        stop_with(a, DFPR_ETIMEOUT);
-        stop = 1;
+    // End of this warp's pass: stop when nothing is flagged and no heavy
+    // gather is open; go on to the next pass while something is flagged;
+    // otherwise help with the open gathers (their vertices may flag more).
+    int next = 0;
+    while (true) {
+      int act = 0;  // 0: help with tokens, 1: stop, 2: next pass
+      if (lane == 0) {
+        if (ld_volatile(&ctl->abort)) {
+          act = 1;
+        } else if (ld_volatile(&ctl->nc.v) > 0) {
+          act = 2;
+          if (timed_out(a)) {
+            stop_with(a, DFPR_ETIMEOUT);
+            act = 1;
+          }
+        } else if (ld_volatile(&ctl->open_tokens.v) <= 0) {
+          act = 1;
+        } else if (timed_out(a)) {
+          stop_with(a, DFPR_ETIMEOUT);
+          act = 1;
+        }
       }
+      act = __shfl_sync(kFull, act, 0);
+      if (act != 0) {
+        next = act == 2;
+        break;
+      }
+      const unsigned long long tok = pop_token(a, lane);
+      if (tok != kNoToken)
+        round_gather_token(a, (unsigned)((tok >> 31) & 0x7fffffffull), (unsigned)(tok & 0x7fffffffull),
+                           lane, s_excl[w], s_off[w], st);
+      else
+        __nanosleep(256);
     }
-    if (__shfl_sync(kFull, stop, 0)) {
+    if (!next) {
       ++pass;
       break;
     }
@@ -1839,7 +1949,9 @@ dfpr_status run_round(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_st
   long long* nsi = nullptr;
   if (kind == kRunDF) nsi = prepare_marking<P>(g, a);
   DFPR_CUDA(cudaEventRecord(e0, s));
-  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 1, 0);
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, 0, 0, 1, g->jcap);
+  DFPR_LAUNCHED();
+  k_init_jobs<<<grid_small(g->jcap), kNT, 0, s>>>(g->job_ring.p, g->jcap);
   DFPR_LAUNCHED();
   g->pass_ctr.ensure((size_t)p.max_iter + 1, s);
   a.pass_ctr = g->pass_ctr.p;
@@ -1874,6 +1986,8 @@ dfpr_status run_round(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_st
   }
   dfpr_status status = h.c.status ? (dfpr_status)h.c.status : DFPR_OK;
   if (status == DFPR_OK && h.c.nc.v > 0) status = DFPR_ENOTCONV;
+  // a run that stopped early can leave exclusion bits and tokens behind
+  if (h.c.status != 0 || h.c.open_tokens.v != 0) reset_worklist_state(g);
   // clear flags and list for the next call
   k_clear_list<<<grid_small(h.c.len.v), kNT, 0, s>>>(g->affected_list.p, h.c.len.v, g->va_bits.p, g->rc_bits.p);
   DFPR_LAUNCHED();
