@@ -234,6 +234,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest x over the ranks of the default process group (x itself when
+    there is none or it has one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_batch(max_total_ms: float, steps: int, ws: int) -> float:
+    """Whole-job ms per batch: every rank ran `steps` batches within the
+    slowest rank's time."""
+    return max_total_ms / (steps * ws)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -320,10 +338,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b_) for a, b_ in ev]
     my_total = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([my_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        my_total = float(t.item())
+    my_total = max_over_ranks(my_total, dev)
     bad = [s for s in stats if s["status"] != dfpr.OK]
 
     # roofline of the persistent DF kernel (the dominant kernel)
@@ -358,7 +373,7 @@ def run_ours(args):
 
     if rank != 0:
         return
-    value = my_total / (args.steps * ws)
+    value = job_ms_per_batch(my_total, args.steps, ws)
     mean = lambda k: float(np.mean([s[k] for s in stats]))  # noqa: E731
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
