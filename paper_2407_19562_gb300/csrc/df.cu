@@ -9,17 +9,21 @@
 // Schedules:
 //  * worklist (persistent kernel, no grid-wide barrier): vertices flagged
 //    not-converged sit in a device queue; a warp pops up to 32, recomputes
-//    them in place, marks out-neighbours when the rank has moved by more than
-//    the frontier tolerance since the vertex last marked them, and re-queues
-//    itself while its change exceeds the iteration tolerance. Each vertex has
-//    a 2-bit state (queued, running) so that no vertex is recomputed by two
-//    warps at once and no update is lost. The iteration ends when the count
-//    of queued + running vertices + open marking items reaches zero.
+//    them in place, marks out-neighbours when the rank moved by more than the
+//    frontier tolerance in this recomputation (or has drifted by more than
+//    ten times that since the vertex last marked them; FP32 mode uses the
+//    drift rule alone), and re-queues itself while its change exceeds the
+//    iteration tolerance. Each vertex has a 2-bit state (queued, running) so
+//    that no vertex is recomputed by two warps at once and no update is lost.
+//    In-rows and out-rows longer than a few thousand edges are cut into
+//    tokens that any warp takes. The iteration ends when the count of queued
+//    + running vertices + open marking items and tokens reaches zero.
 //  * round (Alg. 2): every affected vertex is recomputed in every pass; warps
 //    claim chunks of a pass from a per-pass counter and move to the next pass
 //    without waiting; a per-vertex not-converged flag R_C and its count end
 //    the iteration; marking uses the helping rule (unfinished marking items
-//    are redone by idle warps).
+//    are redone by idle warps); heavy in-rows are cut into gather tokens as
+//    in the worklist.
 //  * jacobi (Alg. 1 / Alg. 3 / Alg. 5): two vectors, one kernel per iteration,
 //    L-inf reduction, swap; marks take effect from the next iteration.
 //
