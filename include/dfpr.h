@@ -134,6 +134,14 @@ typedef struct dfpr_params {
   double fault_delay_us;
   int32_t fault_crash_warps;
   uint32_t fault_seed;
+  /* Degree classes of the worklist and round schedules: an in-row longer
+     than gather_split edges is summed as gather_split-edge tokens that any
+     warp takes, and an out-row longer than mark_split edges is marked the same
+     way; shorter rows are gathered and marked by one warp, edge-balanced over
+     its 32 vertices. 0 selects the defaults (4096 and 8192); otherwise
+     256 <= value <= 2^24. dfpr_autotune picks them by timing. */
+  int32_t gather_split;
+  int32_t mark_split;
 } dfpr_params;
 
 /* Counters of one call. */
@@ -243,6 +251,27 @@ dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_sr
  * (ranks are then valid but not converged), EINVAL for bad parameters.
  */
 dfpr_status dfpr_df_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats);
+
+/*
+ * Autotuner of the degree-class boundaries (no counterpart in the paper):
+ * runs the pending update once per candidate (gather_split, mark_split) pair,
+ * each time from the same ranks and the same pending change set, times the
+ * rank kernel of each trial with CUDA events, then restores that state once
+ * more and runs the update with the fastest pair, which stays applied.
+ * Cost: n_candidates + 1 updates.
+ * p: in, the parameters of every trial (worklist or round mode); out, the
+ * same with gather_split / mark_split set to the chosen pair.
+ * candidates: host, 2 * n_candidates int32 (gather_split, mark_split pairs),
+ * or NULL for the built-in set {(2048, 2048), (4096, 8192), (8192, 8192),
+ * (16384, 16384)} (n_candidates is then ignored).
+ * trial_ms: host, n_candidates doubles (may be NULL): the rank kernel time
+ * of each trial; a trial that did not converge gets +inf.
+ * stats (may be NULL): the final update's counters.
+ * Errors: EINVAL (no pending changes, jacobi mode, bad pair), ENOMEM (no room
+ * for the ranks' snapshot), ECUDA, EBUSY; otherwise the final update's status.
+ */
+dfpr_status dfpr_autotune(dfpr_graph* g, dfpr_params* p, int32_t n_candidates,
+                          const int32_t* candidates, double* trial_ms, dfpr_stats* stats);
 
 /*
  * Naive-dynamic update (Sec. 3.5.1; Alg. 5 / Alg. 6): iterates Eq. 1 over

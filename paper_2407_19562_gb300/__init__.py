@@ -58,7 +58,8 @@ class Params(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("normalize", ctypes.c_int32),
                 ("grid_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
                 ("fault_delay_prob", ctypes.c_double), ("fault_delay_us", ctypes.c_double),
-                ("fault_crash_warps", ctypes.c_int32), ("fault_seed", ctypes.c_uint32)]
+                ("fault_crash_warps", ctypes.c_int32), ("fault_seed", ctypes.c_uint32),
+                ("gather_split", ctypes.c_int32), ("mark_split", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -128,6 +129,7 @@ def load():
                                      ctypes.POINTER(i32)]),
             "dfpr_apply_batch": (st, [vp, i64, vp, vp, i64, vp, vp, ci, ctypes.POINTER(i64)]),
             "dfpr_df_pagerank": (st, [vp, ctypes.POINTER(Params), ctypes.POINTER(Stats)]),
+            "dfpr_autotune": (st, [vp, ctypes.POINTER(Params), i32, vp, vp, ctypes.POINTER(Stats)]),
             "dfpr_nd_pagerank": (st, [vp, ctypes.POINTER(Params), ctypes.POINTER(Stats)]),
             "dfpr_static_pagerank": (st, [vp, ctypes.POINTER(Params), ctypes.POINTER(Stats)]),
             "dfpr_get_ranks": (st, [vp, vp, ci]),
@@ -272,6 +274,9 @@ class Graph:
     def nd_pagerank(self, *a, **k):
         return nd_pagerank(self, *a, **k)
 
+    def autotune(self, *a, **k):
+        return autotune(self, *a, **k)
+
     def static_pagerank(self, *a, **k):
         return static_pagerank(self, *a, **k)
 
@@ -381,6 +386,27 @@ def _run(fn, where, g, params):
 
 def df_pagerank(g: Graph, params: Params | None = None) -> Stats:
     return _run(load().dfpr_df_pagerank, "df_pagerank", g, params)
+
+
+def autotune(g: Graph, params: Params | None = None, candidates=None):
+    """dfpr_autotune: times the pending update under each (gather_split,
+    mark_split) pair and leaves it applied with the fastest one. Returns
+    (tuned Params, trial times in ms, Stats of the final update)."""
+    p = Params.from_buffer_copy(params if params is not None else default_params())
+    if candidates is None:
+        k, cand, n_trials = 0, None, 4
+    else:
+        arr = np.ascontiguousarray(np.asarray(candidates, np.int32).reshape(-1, 2))
+        k, cand, n_trials = len(arr), arr, len(arr)
+    trials = np.zeros(n_trials, np.float64)
+    st = Stats()
+    rc = load().dfpr_autotune(g.handle, ctypes.byref(p), k,
+                              cand.ctypes.data if cand is not None else None,
+                              trials.ctypes.data, ctypes.byref(st))
+    if rc not in (OK, ENOTCONV, ETIMEOUT):
+        _check(rc, "autotune")
+    st.status = rc
+    return p, trials, st
 
 
 def nd_pagerank(g: Graph, params: Params | None = None) -> Stats:

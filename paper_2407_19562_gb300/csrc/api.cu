@@ -134,6 +134,10 @@ void check_params(const dfpr_params& p) {
   DFPR_REQUIRE(p.fault_delay_us >= 0.0 && p.fault_delay_us <= 1e6, DFPR_EINVAL,
                "fault_delay_us must lie in [0, 1e6]");
   DFPR_REQUIRE(p.fault_crash_warps >= 0, DFPR_EINVAL, "fault_crash_warps must be >= 0");
+  DFPR_REQUIRE(p.gather_split == 0 || (p.gather_split >= 256 && p.gather_split <= (1 << 24)),
+               DFPR_EINVAL, "gather_split must be 0 or lie in [256, 2^24]");
+  DFPR_REQUIRE(p.mark_split == 0 || (p.mark_split >= 256 && p.mark_split <= (1 << 24)),
+               DFPR_EINVAL, "mark_split must be 0 or lie in [256, 2^24]");
   DFPR_REQUIRE(!(p.fault_crash_warps > 0 && p.mode == DFPR_MODE_JACOBI), DFPR_EINVAL,
                "crash-stop faults need a lock-free schedule: the jacobi schedule's iteration "
                "barrier would never complete (Sec. 5.4)");
@@ -216,6 +220,8 @@ void dfpr_default_params(dfpr_params* p) {
   p->fault_delay_us = 0.0;
   p->fault_crash_warps = 0;
   p->fault_seed = 0u;
+  p->gather_split = 0;
+  p->mark_split = 0;
 }
 
 int32_t dfpr_version(void) { return 100; }
@@ -450,6 +456,73 @@ dfpr_status dfpr_df_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* st
   BusyGuard bg(g);
   DeviceGuard dg(g->device);
   return run_update(g, p, stats, kRunDF);
+  API_END
+}
+
+dfpr_status dfpr_autotune(dfpr_graph* g, dfpr_params* p, int32_t n_candidates,
+                          const int32_t* candidates, double* trial_ms, dfpr_stats* stats) {
+  static const int32_t kDefaultPairs[8] = {2048, 2048, 4096, 8192, 8192, 8192, 16384, 16384};
+  if (!g || !p || (candidates && n_candidates < 1)) {
+    set_error("dfpr_autotune: need a graph, parameters and at least one candidate");
+    return DFPR_EINVAL;
+  }
+  const int32_t* cand = candidates ? candidates : kDefaultPairs;
+  const int32_t k = candidates ? n_candidates : 4;
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  DFPR_REQUIRE(p->mode != DFPR_MODE_JACOBI, DFPR_EINVAL,
+               "dfpr_autotune: the split thresholds apply to the worklist and round schedules");
+  DFPR_REQUIRE(g->pend.n_src > 0 || g->pend.n_dst > 0, DFPR_EINVAL,
+               "dfpr_autotune: no pending changes to time the candidates on");
+  for (int32_t i = 0; i < k; ++i) {
+    dfpr_params q = *p;
+    q.gather_split = cand[2 * i];
+    q.mark_split = cand[2 * i + 1];
+    check_params(q);
+  }
+  cudaStream_t s = g->stream;
+  const long long n_src = g->pend.n_src, n_dst = g->pend.n_dst;
+  const bool fp64 = g->cfg.precision == DFPR_FP64;
+  const size_t rb = sizeof(double) * (size_t)g->n, cb = sizeof(long long) * (size_t)g->n;
+  const size_t rb32 = sizeof(float) * (size_t)g->n;
+  void* R = fp64 ? (void*)g->R64.p : (void*)g->R32.p;
+  void* C = fp64 ? (void*)g->C64.p : (void*)g->C32.p;
+  const size_t r_bytes = fp64 ? rb : rb32, c_bytes = fp64 ? cb : rb32;
+  DevArray<unsigned char> snap;  // the ranks and contributions every trial starts from
+  snap.reset(r_bytes + c_bytes, s);
+  DFPR_CUDA(cudaMemcpyAsync(snap.p, R, r_bytes, cudaMemcpyDeviceToDevice, s));
+  DFPR_CUDA(cudaMemcpyAsync(snap.p + r_bytes, C, c_bytes, cudaMemcpyDeviceToDevice, s));
+  auto restore = [&]() {
+    DFPR_CUDA(cudaMemcpyAsync(R, snap.p, r_bytes, cudaMemcpyDeviceToDevice, s));
+    DFPR_CUDA(cudaMemcpyAsync(C, snap.p + r_bytes, c_bytes, cudaMemcpyDeviceToDevice, s));
+    g->pend.n_src = n_src;  // the pending arrays are left intact by an update
+    g->pend.n_dst = n_dst;
+  };
+  double best = INFINITY;
+  int32_t bi = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    if (i > 0) restore();
+    dfpr_params q = *p;
+    q.gather_split = cand[2 * i];
+    q.mark_split = cand[2 * i + 1];
+    dfpr_stats st;
+    const dfpr_status r = run_update(g, &q, &st, kRunDF);
+    const double ms = r == DFPR_OK ? st.ms : INFINITY;
+    if (trial_ms) trial_ms[i] = ms;
+    if (ms < best) {
+      best = ms;
+      bi = i;
+    }
+  }
+  restore();
+  p->gather_split = cand[2 * bi];
+  p->mark_split = cand[2 * bi + 1];
+  dfpr_stats st;
+  const dfpr_status r = run_update(g, p, &st, kRunDF);
+  if (stats) *stats = st;
+  DFPR_CUDA(cudaStreamSynchronize(s));
+  return r;
   API_END
 }
 

@@ -234,6 +234,8 @@ struct Args {
   int teleport;
   unsigned long long timeout_ns;
   int mark_only;
+  int gather_split;  // in-edges per gather token (longer in-rows are split)
+  int mark_split;    // out-edges per mark token (longer out-rows are split)
   // simulated faults (Sec. 5.1.6): per-vertex delay probability as a 64-bit
   // threshold, delay length, crashing warps = those whose slot in a seeded
   // permutation of the launch's warps is below fault_crash_warps
@@ -553,10 +555,12 @@ __device__ __forceinline__ bool mark_one(const Args<P>& a, int t, bool valid, un
 
 // Tokens: bit 63..62 kind, 61..31 a, 30..0 b. Kind 0: gather chunk b of job
 // slot a. Kind 1: mark chunk b of vertex a's out-row.
-// In-edges per gather token and out-edges per mark token; longer rows are
-// split. Measured on R-MAT scale 24: 4096 / 8192 took 107 ms per update,
-// 2048 / 2048 115 ms, 1024 / 1024 182 ms (token and job overhead), and
-// 16384 / 16384 138 ms (too few pieces to spread a hub over the GPU).
+// Default in-edges per gather token and out-edges per mark token (longer
+// rows are split; dfpr_params.gather_split / mark_split override them, and
+// dfpr_autotune picks them by timing). Measured on R-MAT scale 24: 4096 /
+// 8192 took 107 ms per update, 2048 / 2048 115 ms, 1024 / 1024 182 ms (token
+// and job overhead), and 16384 / 16384 138 ms (too few pieces to spread a
+// hub over the GPU).
 constexpr int kGatherChunk = 4096;
 constexpr int kMarkSplit = 8192;
 constexpr unsigned long long kNoToken = ~0ull;
@@ -673,13 +677,13 @@ __device__ void free_job(const Args<P>& a, int id) {
 }
 
 // Marks the out-neighbours of every lane's vertex v (with od > 0 out-edges at
-// oo). Out-rows longer than kMarkSplit become mark tokens that any warp takes;
+// oo). Out-rows longer than a.mark_split become mark tokens that any warp takes;
 // the rest are walked edge-balanced, kUnroll chunks in flight.
 template <class P>
 __device__ void expand_rows(const Args<P>& a, int v, int od, long long oo, int lane, int* s_excl,
                             long long* s_off, PushBuf pb, WarpStats& st) {
-  const bool split = od > kMarkSplit;
-  push_tokens(a, split ? (od + kMarkSplit - 1) / kMarkSplit : 0, 1u, (unsigned)max(v, 0), lane, st,
+  const bool split = od > a.mark_split;
+  push_tokens(a, split ? (od + a.mark_split - 1) / a.mark_split : 0, 1u, (unsigned)max(v, 0), lane, st,
               &a.ctl->pending.v);
   if (split) od = 0;
   int incl = od;
@@ -860,8 +864,8 @@ __device__ bool sum_gather_token(const Args<P>& a, unsigned slot, unsigned chunk
   fence_acq_rel();  // the job record was published before the token
   const int v = ld_volatile(a.job_v + slot);
   const RowDesc row = load_row(a.in_rows + v);
-  const long long beg = (long long)chunk * kGatherChunk;
-  const long long end = min((long long)row.deg, beg + kGatherChunk);
+  const long long beg = (long long)chunk * a.gather_split;
+  const long long end = min((long long)row.deg, beg + a.gather_split);
   typename P::acc acc = P::zero();
   for (long long e0 = beg; e0 < end; e0 += 32 * kUnroll) {
     typename P::contrib xv[kUnroll];
@@ -925,8 +929,8 @@ template <class P>
 __device__ void run_mark_token(const Args<P>& a, unsigned u, unsigned chunk, int lane, PushBuf pb,
                                WarpStats& st) {
   const RowDesc r = load_row(a.out_rows + u);
-  const long long beg = (long long)chunk * kMarkSplit;
-  const long long end = min((long long)r.deg, beg + kMarkSplit);
+  const long long beg = (long long)chunk * a.mark_split;
+  const long long end = min((long long)r.deg, beg + a.mark_split);
   for (long long e0 = beg; e0 < end; e0 += 32 * kUnroll) {
     int t[kUnroll];
 #pragma unroll
@@ -1086,10 +1090,10 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       int nch = 0, slot = -1;
       if (v >= 0) {
         const int din = load_row(a.in_rows + v).deg;
-        if (din > kGatherChunk) {
+        if (din > a.gather_split) {
           slot = alloc_job(a);
           if (slot >= 0) {
-            nch = (din + kGatherChunk - 1) / kGatherChunk;
+            nch = (din + a.gather_split - 1) / a.gather_split;
             a.job_v[slot] = v;
             a.job_sum[slot] = 0ull;
             a.job_rem[slot] = nch;
@@ -1390,10 +1394,10 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
       // that sums its last chunk finishes it.
       {
         int nch = 0, slot = -1;
-        if (v >= 0 && irow.deg > kGatherChunk) {
+        if (v >= 0 && irow.deg > a.gather_split) {
           slot = alloc_job(a);
           if (slot >= 0) {
-            nch = (irow.deg + kGatherChunk - 1) / kGatherChunk;
+            nch = (irow.deg + a.gather_split - 1) / a.gather_split;
             a.job_v[slot] = v;
             a.job_sum[slot] = 0ull;
             a.job_rem[slot] = nch;
@@ -1773,6 +1777,8 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   a.teleport = g->cfg.dead_end == DFPR_TELEPORT;
   const double tmo = p.timeout_ms > 0 ? p.timeout_ms : 60000.0;
   a.timeout_ns = (unsigned long long)(tmo * 1e6);
+  a.gather_split = p.gather_split > 0 ? p.gather_split : kGatherChunk;
+  a.mark_split = p.mark_split > 0 ? p.mark_split : kMarkSplit;
   a.fault_seed = host_mix64(0x243f6a8885a308d3ull ^ (unsigned long long)p.fault_seed);
   a.fault_delay_thr = p.fault_delay_prob >= 1.0 ? ~0ull
                       : (unsigned long long)(p.fault_delay_prob * 18446744073709551616.0);

@@ -53,6 +53,7 @@ int main(void) {
          sizeof(dfpr_stats));
   F(dfpr_graph_config, tail_slack); F(dfpr_params, timeout_ms); F(dfpr_params, grid_ctas);
   F(dfpr_params, fault_delay_prob); F(dfpr_params, fault_crash_warps); F(dfpr_params, fault_seed);
+  F(dfpr_params, gather_split); F(dfpr_params, mark_split);
   F(dfpr_stats, passes); F(dfpr_stats, residual_linf); F(dfpr_stats, ms);
   return 0;
 }
@@ -67,7 +68,7 @@ int main(void) {
     assert int(got["dfpr_graph_config.tail_slack"]) == dfpr.Config.tail_slack.offset
     assert int(got["dfpr_params.timeout_ms"]) == dfpr.Params.timeout_ms.offset
     assert int(got["dfpr_params.grid_ctas"]) == dfpr.Params.grid_ctas.offset
-    for f in ("fault_delay_prob", "fault_crash_warps", "fault_seed"):
+    for f in ("fault_delay_prob", "fault_crash_warps", "fault_seed", "gather_split", "mark_split"):
         assert int(got[f"dfpr_params.{f}"]) == getattr(dfpr.Params, f).offset
     assert int(got["dfpr_stats.passes"]) == dfpr.Stats.passes.offset
     assert int(got["dfpr_stats.residual_linf"]) == dfpr.Stats.residual_linf.offset
@@ -99,6 +100,7 @@ def test_host_side_argument_errors():
                                ctypes.byref(h)) == dfpr.EINVAL
     assert lib.dfpr_apply_batch(None, 0, None, None, 0, None, None, 0, None) == dfpr.EINVAL
     assert lib.dfpr_df_pagerank(None, None, None) == dfpr.EINVAL
+    assert lib.dfpr_autotune(None, None, 0, None, None, None) == dfpr.EINVAL
     assert lib.dfpr_get_ranks(None, None, 0) == dfpr.EINVAL
     assert lib.dfpr_graph_free(None) == dfpr.OK
     assert lib.dfpr_set_allocator(dfpr.ALLOC_FN(lambda *a: None), dfpr.FREE_FN(), None) == dfpr.EINVAL
