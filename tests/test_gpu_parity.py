@@ -399,3 +399,47 @@ def test_caller_numbering_kept_with_and_without_reorder(gpu_lib, c1, reorder):
     st = g.df_pagerank()
     assert st.status == gpu_lib.OK
     assert np.max(np.abs(g.get_ranks() - c1["ref1"])) <= LINF64
+
+
+# --------------------------------------------------------------------------
+# Batch sizes at the ends of the range
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", MODES)
+def test_df_large_batch(gpu_lib, c1, mode):
+    """A batch of 10 % of the edges (the top of the swept range): most
+    vertices are affected; every schedule still lands on the reference."""
+    n, src, dst = c1["n"], c1["src"], c1["dst"]
+    batch = workloads.uniform_batch(n, 26000, 41, src, dst)
+    g1, nreal = c1["g0"].apply(*batch)
+    ref1, _ = g1.reference()
+    g = gpu_lib.graph_load(n, src, dst)
+    g.set_ranks(c1["R0ref"])
+    assert g.apply_batch(*batch) == nreal
+    check_graph(g, g1)
+    st = g.df_pagerank(gpu_lib.default_params(mode=getattr(gpu_lib, mode)))
+    assert st.status == gpu_lib.OK
+    assert np.max(np.abs(g.get_ranks() - ref1)) <= LINF64
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,edges,batch", [
+    (1, [], ([], [], [], [])),                          # one vertex, only its self-loop
+    (2, [(0, 1)], ([0], [1], [1], [0])),                 # the only edge turns around
+    (5, [(0, 1), (1, 2), (2, 3), (3, 4)], ([1], [2], [4, 4], [0, 2])),
+])
+def test_df_tiny_graphs(gpu_lib, mode, n, edges, batch):
+    src = np.array([e[0] for e in edges], np.int32)
+    dst = np.array([e[1] for e in edges], np.int32)
+    b = tuple(np.array(x, np.int32) for x in batch)
+    g0 = oracle.Graph.build(n, src, dst)
+    R0, _ = g0.reference()
+    g1, nreal = g0.apply(*b)
+    ref1, _ = g1.reference()
+    g = gpu_lib.graph_load(n, src, dst)
+    g.set_ranks(R0)
+    assert g.apply_batch(*b) == nreal
+    check_graph(g, g1)
+    st = g.df_pagerank(gpu_lib.default_params(mode=getattr(gpu_lib, mode)))
+    assert st.status == gpu_lib.OK
+    assert np.max(np.abs(g.get_ranks() - ref1)) <= LINF64
