@@ -139,7 +139,9 @@ typedef struct dfpr_params {
      warp takes, and an out-row longer than mark_split edges is marked the same
      way; shorter rows are gathered and marked by one warp, edge-balanced over
      its 32 vertices. 0 selects the defaults (4096 and 8192); otherwise
-     256 <= value <= 2^24. dfpr_autotune picks them by timing. */
+     max(256, edges / 2^20) <= value <= 2^24, so that the tokens of a launch
+     fit the device's token ring (2^21 entries). dfpr_autotune picks them by
+     timing. */
   int32_t gather_split;
   int32_t mark_split;
 } dfpr_params;

@@ -3,6 +3,7 @@
 // point catches the library's internal failures and returns a status.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -156,6 +157,14 @@ dfpr_status run_update(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, Run
   if (g->cfg.dead_end == DFPR_TELEPORT)
     DFPR_REQUIRE(p.mode == DFPR_MODE_JACOBI, DFPR_EINVAL,
                  "teleport dead-end handling is supported by the jacobi schedule only");
+  {
+    // a launch's gather (and mark) tokens must fit half the token ring each
+    const long long min_split = std::max<long long>(256, (g->m + (1ll << 20) - 1) >> 20);
+    DFPR_REQUIRE(p.gather_split == 0 || p.gather_split >= min_split, DFPR_EINVAL,
+                 "gather_split must be at least max(256, edges / 2^20)");
+    DFPR_REQUIRE(p.mark_split == 0 || p.mark_split >= min_split, DFPR_EINVAL,
+                 "mark_split must be at least max(256, edges / 2^20)");
+  }
   dfpr_stats local;
   memset(&local, 0, sizeof local);
   local.rank_sum = NAN;
