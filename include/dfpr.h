@@ -134,14 +134,14 @@ typedef struct dfpr_params {
   double fault_delay_us;
   int32_t fault_crash_warps;
   uint32_t fault_seed;
-  /* Degree classes of the worklist and round schedules: an in-row longer
-     than gather_split edges is summed as gather_split-edge tokens that any
-     warp takes, and an out-row longer than mark_split edges is marked the same
-     way; shorter rows are gathered and marked by one warp, edge-balanced over
-     its 32 vertices. 0 selects the defaults (4096 and 8192); otherwise
-     max(256, edges / 2^20) <= value <= 2^24, so that the tokens of a launch
-     fit the device's token ring (2^21 entries). dfpr_autotune picks them by
-     timing. */
+  /* Degree classes: an in-row longer than gather_split edges is summed as
+     gather_split-edge tokens that any warp takes (worklist and round
+     schedules), and an out-row longer than mark_split edges is marked the
+     same way (worklist schedule); shorter rows are gathered and marked by one
+     warp, edge-balanced over its 32 vertices. 0 selects the defaults (4096
+     and 8192); otherwise max(256, edges / 2^20) <= value <= 2^24, so that
+     the tokens of a launch fit the device's token ring (2^21 entries).
+     dfpr_autotune picks them by timing. */
   int32_t gather_split;
   int32_t mark_split;
 } dfpr_params;
@@ -247,8 +247,9 @@ dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_sr
  * its rank moved by more than tau_f (Alg. 1, Alg. 2). The worklist schedule
  * recomputes only marked vertices, so there a vertex also marks them once its
  * rank has drifted by more than 10 tau_f since it last did (in FP32 mode:
- * by more than tau_f, the only rule), which bounds what a dependant misses. With no pending changes it returns at once with 0
- * recomputations. p NULL selects the defaults; stats may be NULL.
+ * by more than tau_f, the only rule), which bounds what a dependant misses.
+ * With no pending changes it returns at once with 0 recomputations. p NULL
+ * selects the defaults; stats may be NULL.
  * Returns ENOTCONV / ETIMEOUT when the cap / budget stopped the iteration
  * (ranks are then valid but not converged), EINVAL for bad parameters.
  */
