@@ -13,6 +13,13 @@
  *
  * Conventions for every entry point:
  *  - Vertex ids are int32 in [0, n). Edge counts and offsets are int64.
+ *  - Size limits: a graph (or a set) holds at most 2^32 - 2 edges, self-loops
+ *    included, since edge keys are counted with 32-bit prefix sums
+ *    (dfpr_graph_load and dfpr_apply_batch return EINVAL beyond it). The
+ *    update calls (static, ND, DF, autotune) need every in- and out-degree at
+ *    most 2^25 - 1, since a warp adds the degrees of its 32 rows in 32-bit
+ *    integers; they return EINVAL otherwise. Degrees are tracked only when n
+ *    exceeds 2^25 - 1 (a degree never exceeds n).
  *  - Pointer arguments marked "host or device" are host pointers when
  *    on_device == 0 and device pointers of the graph's device when
  *    on_device != 0. The library copies inputs before returning; the caller
@@ -180,7 +187,8 @@ void dfpr_default_params(dfpr_params* p);
  * Ranks start at 1/n (Sec. 3.1). cuda_stream is a cudaStream_t (NULL: the
  * library creates one). cfg NULL selects the defaults. On success *out owns
  * the graph until dfpr_graph_free. Errors: EINVAL (n <= 0, m < 0, null
- * arrays with m > 0, an id out of range), ENOMEM, ECUDA.
+ * arrays with m > 0, more than 2^32 - 2 edges with the self-loops, an id out
+ * of range; the size check comes before the arrays are read), ENOMEM, ECUDA.
  */
 dfpr_status dfpr_graph_load(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                             int on_device, void* cuda_stream, const dfpr_graph_config* cfg,
@@ -231,8 +239,9 @@ dfpr_status dfpr_graph_info(const dfpr_graph* g, int32_t* n, int64_t* m, int32_t
  * next dfpr_df_pagerank, which marks the out-neighbours of their sources
  * (Sec. 4.1). n_applied (host, may be NULL) receives {|Delta-|, |Delta+|}.
  * Arrays are host or device. Applying a second batch before dfpr_df_pagerank
- * merges both into the pending change set. Errors: EINVAL (an id out of range;
- * the graph is left unchanged), ENOMEM, ECUDA, EBUSY.
+ * merges both into the pending change set. Errors: EINVAL (an id out of range,
+ * or n_del + n_ins or the graph's edges plus n_ins above 2^32 - 2; the graph
+ * is left unchanged), ENOMEM, ECUDA, EBUSY.
  */
 dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_src,
                              const int32_t* del_dst, int64_t n_ins, const int32_t* ins_src,
@@ -251,7 +260,8 @@ dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_sr
  * With no pending changes it returns at once with 0 recomputations. p NULL
  * selects the defaults; stats may be NULL.
  * Returns ENOTCONV / ETIMEOUT when the cap / budget stopped the iteration
- * (ranks are then valid but not converged), EINVAL for bad parameters.
+ * (ranks are then valid but not converged), EINVAL for bad parameters or a
+ * vertex whose in- or out-degree exceeds 2^25 - 1 (ranks untouched).
  */
 dfpr_status dfpr_df_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats);
 

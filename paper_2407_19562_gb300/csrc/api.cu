@@ -152,6 +152,8 @@ dfpr_status run_update(dfpr_graph* g, const dfpr_params* pp, dfpr_stats* st, Run
   if (pp) p = *pp;
   else dfpr_default_params(&p);
   check_params(p);
+  DFPR_REQUIRE(g->max_degree <= kDegreeLimit, DFPR_EINVAL,
+               "a vertex has more than 2^25 - 1 in- or out-edges, the update kernels' limit");
   DFPR_REQUIRE(!(p.normalize && g->nparts > 1), DFPR_EINVAL,
                "normalize is not supported for a set of graphs");
   if (g->cfg.dead_end == DFPR_TELEPORT)
@@ -271,6 +273,10 @@ static dfpr_status load_impl(int32_t n, int64_t m, const int32_t* src, const int
       (c.dead_end != DFPR_SELF_LOOPS && c.dead_end != DFPR_TELEPORT) || c.row_slack < 0 ||
       c.min_slack < 0 || c.tail_slack < 0) {
     set_error("dfpr_graph_load: invalid config");
+    return DFPR_EINVAL;
+  }
+  if (m + (c.dead_end == DFPR_SELF_LOOPS ? (long long)n : 0ll) > kEdgeLimit) {
+    set_error("dfpr_graph_load: a graph holds at most 2^32 - 2 edges, self-loops included");
     return DFPR_EINVAL;
   }
   if (k > 1 && c.dead_end == DFPR_TELEPORT) {
@@ -435,6 +441,8 @@ dfpr_status dfpr_apply_batch(dfpr_graph* g, int64_t n_del, const int32_t* del_sr
   }
   API_BEGIN
   BusyGuard bg(g);
+  DFPR_REQUIRE(n_del + n_ins <= kEdgeLimit && g->m + n_ins <= kEdgeLimit, DFPR_EINVAL,
+               "dfpr_apply_batch: a batch, and a graph after it, hold at most 2^32 - 2 edges");
   DeviceGuard dg(g->device);
   DevArray<int32_t> a, b, c, d;
   const int32_t* ds = stage_in(g, a, del_src, n_del, on_device);

@@ -263,6 +263,7 @@ struct dfpr_graph {
   dfpr::DevArray<int32_t> perm;           // caller id -> internal id (when reordered)
   dfpr::DevArray<int32_t> iperm;          // internal id -> caller id
   bool relabeled = false;
+  long long max_degree = -1;              // largest in- or out-degree, when tracked
   dfpr::Pending pend;
   dfpr::Scratch scratch;
   dfpr::DevArray<unsigned long long> host_sync;  // small device words read back

@@ -24,7 +24,8 @@ enum {
 };
 
 // Device words of g->host_sync.
-enum { kWErr = 0, kWRealDel = 1, kWRealIns = 2, kWOverflow = 3, kWNGroups = 4, kWS = 5, kWW = 6 };
+enum { kWErr = 0, kWRealDel = 1, kWRealIns = 2, kWOverflow = 3, kWNGroups = 4, kWS = 5, kWW = 6,
+       kWMaxDeg = 7 };
 
 namespace {
 
@@ -488,6 +489,14 @@ __global__ void k_offsets_from_bounds(const long long* __restrict__ first,
   GRID_STRIDE(u, n) deg[u] = last[u] - first[u];
 }
 
+// Largest degree over the rows of one direction, folded into *out.
+__global__ void k_max_degree(const RowDesc* __restrict__ rows, int32_t n, unsigned long long* out) {
+  unsigned long long d = 0;
+  GRID_STRIDE(u, n) d = max(d, (unsigned long long)rows[u].deg);
+  for (int k = 16; k > 0; k >>= 1) d = max(d, __shfl_down_sync(0xffffffffu, d, k));
+  if ((threadIdx.x & 31) == 0 && d > 0) atomicMax(out, d);
+}
+
 unsigned grid_for(long long n) { return blocks_for(n, NT, 152u * 32u); }
 
 }  // namespace
@@ -777,6 +786,7 @@ void graph_build(dfpr_graph* g, const int32_t* src, const int32_t* dst, long lon
   unsigned long long* t_sorted = radix_sort_u64(sorted, other, m, 2 * g->bits, sc, s);
   build_direction(g, g->in, t_sorted, m);
   g->m = m;
+  track_max_degree(g);
 }
 
 void graph_apply(dfpr_graph* g, const int32_t* ds, const int32_t* dd, long long nd,
@@ -833,6 +843,7 @@ void graph_apply(dfpr_graph* g, const int32_t* ds, const int32_t* dd, long long 
   unsigned long long* rcs = radix_sort_u64(rct, rct2, nrc, b3, sc, s);
   apply_direction(g, g->in, rcs, nrc, false);
   g->m += n_applied[1] - n_applied[0];
+  track_max_degree(g);
 }
 
 void graph_export(dfpr_graph* g, const Rows& dir, long long* offsets, int32_t* idx) {
@@ -873,6 +884,21 @@ void graph_export(dfpr_graph* g, const Rows& dir, long long* offsets, int32_t* i
   k_export_rows<<<grid_for(32ll * n), NT, 0, s>>>(dir.rows.p, dir.edges.p, n, offsets, idx,
                                                    nullptr, g->bits);
   DFPR_LAUNCHED();
+}
+
+void track_max_degree(dfpr_graph* g) {
+  if ((long long)g->n <= kDegreeLimit) {
+    g->max_degree = -1;
+    return;
+  }
+  cudaStream_t s = g->stream;
+  unsigned long long* w = g->host_sync.p + kWMaxDeg;
+  DFPR_CUDA(cudaMemsetAsync(w, 0, sizeof(unsigned long long), s));
+  k_max_degree<<<grid_for(g->n), NT, 0, s>>>(g->out.rows.p, g->n, w);
+  DFPR_LAUNCHED();
+  k_max_degree<<<grid_for(g->n), NT, 0, s>>>(g->in.rows.p, g->n, w);
+  DFPR_LAUNCHED();
+  g->max_degree = (long long)read_word(g, w, sizeof(unsigned long long));
 }
 
 void refresh_contributions(dfpr_graph* g) {

@@ -106,6 +106,27 @@ def test_host_side_argument_errors():
     assert lib.dfpr_set_allocator(dfpr.ALLOC_FN(lambda *a: None), dfpr.FREE_FN(), None) == dfpr.EINVAL
 
 
+def test_edge_limit_is_checked_before_the_edges_are_read():
+    """Edge keys are counted with 32-bit prefix sums, so a graph holds at most
+    2^32 - 2 edges, self-loops included. A larger load is rejected before the
+    edge arrays are read (the two-element arrays here would not cover it)."""
+    lib = dfpr.load()
+    h = ctypes.c_void_p()
+    src = np.array([0, 1], np.int32)
+    limit = (1 << 32) - 2
+    n = 4
+    # self-loops (the default) add n edges
+    assert lib.dfpr_graph_load(n, limit - n + 1, src.ctypes.data, src.ctypes.data, 0, None, None,
+                               ctypes.byref(h)) == dfpr.EINVAL
+    assert "2^32 - 2 edges" in dfpr.last_error()
+    tele = dfpr.default_config(dead_end=dfpr.TELEPORT)
+    assert lib.dfpr_graph_load(n, limit + 1, src.ctypes.data, src.ctypes.data, 0, None,
+                               ctypes.byref(tele), ctypes.byref(h)) == dfpr.EINVAL
+    assert lib.dfpr_graph_load(n, 1 << 40, src.ctypes.data, src.ctypes.data, 0, None, None,
+                               ctypes.byref(h)) == dfpr.EINVAL
+    assert not h.value
+
+
 def test_binding_rejects_mismatched_arrays():
     with pytest.raises(dfpr.DfprError):
         dfpr._ptr(np.zeros(3, np.int64), np.int32)
