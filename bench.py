@@ -201,24 +201,52 @@ def load_peaks():
 # CPU oracle baseline (bounded sample)
 # --------------------------------------------------------------------------
 
-def oracle_sample(scale: int, batch_frac: float, steps: int, seed0: int = 100):
-    """Times the oracle's apply + DF_LF (one core) on an R-MAT graph of the
-    given scale from the same generator; returns per-step ms and a description."""
+def sample_spec(spec, cpu_scale: int):
+    """The bounded sample of a workload the oracle is timed on: the same
+    generator, edge factor and seed at R-MAT scale `cpu_scale`, or a grid of
+    side 2^(cpu_scale / 2); and the ratio of the workload's edge draws to the
+    sample's."""
+    if spec["kind"] == "rmat":
+        s = dict(spec, scale=min(cpu_scale, spec["scale"]))
+        return s, float(2 ** (spec["scale"] - s["scale"]))
+    L = min(1 << (cpu_scale // 2), spec["L"])
+    return dict(spec, L=L), (spec["L"] / L) ** 2
+
+
+def oracle_sample(spec, cpu_scale: int, batch_frac: float, steps: int, seed0: int = 100):
+    """Times the oracle's apply + DF_LF (one core) on the bounded sample of a
+    workload. Returns per-step ms of the sample, the factor that scales them
+    to the workload, and a description. The batch is a fixed fraction of
+    |E|, so the work of an update grows with |E|; the oracle's time per edge
+    grows too as its arrays outgrow the CPU caches, so the scaled figure is a
+    lower bound on the oracle's time at the workload's size."""
     import oracle
-    n, src, dst = workloads.rmat_graph(scale, 16, 3)
+    sspec, factor = sample_spec(spec, cpu_scale)
+    n, src, dst = make_graph(sspec)
     g = oracle.Graph.build(n, src, dst)
     R, _ = g.static_bb(tol=1e-13)  # R^0 converged to the frontier tolerance
     b = max(1, int(round(batch_frac * g.m)))
     times = []
     for i in range(steps):
-        batch = workloads.uniform_batch(n, b, seed0 + i, src, dst)
+        batch = make_batch(sspec, n, src, dst, b, seed0 + i)
         t0 = time.perf_counter()
         g, _ = g.apply(*batch)
         R, _ = g.df_lf(R)
         times.append((time.perf_counter() - t0) * 1e3)
-    desc = (f"oracle apply + DF_LF (Alg. 2, one thread) on R-MAT scale {scale} "
-            f"(n={n}, m={g.m}), batches of {b} edges ({batch_frac:g}|E|, 80/20)")
-    return times, desc
+    what = (f"R-MAT scale {sspec['scale']}, edge factor {sspec['edge_factor']}"
+            if sspec["kind"] == "rmat" else f"grid {sspec['L']} x {sspec['L']}")
+    desc = (f"oracle apply + DF_LF (Alg. 2, one thread) on {what} (n={n}, m={g.m}), batches of "
+            f"{b} edges ({batch_frac:g}|E|, 80/20); ms/batch scaled by {factor:g}, the ratio of "
+            f"the workload's edge draws to the sample's (a lower bound: the oracle's time per "
+            f"edge grows with the graph)")
+    return times, factor, desc
+
+
+def cpu_baseline_entry(times, factor, desc, cores=1):
+    sample_ms = statistics.mean(times)
+    return {"value": sample_ms * factor, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": desc, "sample_ms_per_batch": sample_ms, "scale_factor": factor,
+            "cpu": cpu_model()}
 
 
 def cpu_model():
@@ -265,17 +293,23 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    times, desc = oracle_sample(args.cpu_scale, args.batch_frac, args.warmup + args.steps)
-    timed = times[args.warmup:]
-    v = statistics.mean(timed)
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the oracle baseline covers the single-graph workloads, not {args.workload}"}),
+              flush=True)
+        return
+    spec = WORKLOADS[args.workload]
+    times, factor, desc = oracle_sample(spec, args.cpu_scale, args.batch_frac,
+                                        args.warmup + args.steps)
+    cpu = cpu_baseline_entry(times[args.warmup:], factor, desc)
+    v = cpu["value"]
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"rmat{args.cpu_scale}-ef16-batch{args.batch_frac:g}",
-                   "precision": "fp64"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                         "cpu": cpu_model()},
+        "config": {"workload": f"{args.workload}-batch{args.batch_frac:g}", "insert_frac": 0.8,
+                   "precision": "fp64", "alpha": 0.85, "tol": 1e-10},
+        "cpu_baseline": cpu,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -378,9 +412,8 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        times, desc = oracle_sample(args.cpu_scale, args.batch_frac, 2)
-        cpu = {"value": statistics.mean(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": desc, "cpu": cpu_model()}
+        times, factor, desc = oracle_sample(spec, args.cpu_scale, args.batch_frac, 2)
+        cpu = cpu_baseline_entry(times, factor, desc)
 
     if rank != 0:
         if ws > 1:
