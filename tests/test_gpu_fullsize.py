@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size: R-MAT scale 24 (16.8M vertices, 280M
-edges with self-loops), one batch of 1e-4 |E|, FP64, worklist schedule, the
-default launch configuration the benchmark times.
+edges with self-loops), one batch of 1e-4 |E|, worklist schedule, the
+default launch configuration the benchmark times; FP64, and FP32 with a
+relative residual bound (last test).
 
 The oracle cannot build this graph or compute its reference ranks in a test's
 time, so it checks what it can compute one vertex at a time, straight from
@@ -46,6 +47,19 @@ def full():
     return dict(n=n, src=src, dst=dst, batch=batch, sample=sample, resid=resid)
 
 
+def eq1_inputs(full):
+    """In-rows of the residual sample and the out-degrees of their sources,
+    from the oracle's row sampler (computed once per module)."""
+    if "rin" not in full:
+        n, src, dst, batch = full["n"], full["src"], full["dst"], full["batch"]
+        rin = oracle.sample_rows(n, src, dst, full["resid"], "in", batch=batch)
+        nbrs = np.unique(np.concatenate(rin)).astype(np.int32)
+        rows = oracle.sample_rows(n, src, dst, nbrs, "out", batch=batch, cap=1 << 26)
+        full["rin"], full["nbrs"] = rin, nbrs
+        full["nbr_deg"] = np.array([len(r) for r in rows], np.float64)
+    return full["resid"], full["rin"], full["nbrs"], full["nbr_deg"]
+
+
 def test_full_size_rows_and_eq1_residual(gpu_lib, full):
     n, src, dst, batch, sample = full["n"], full["src"], full["dst"], full["batch"], full["sample"]
     g = gpu_lib.graph_load(n, src, dst)
@@ -69,11 +83,7 @@ def test_full_size_rows_and_eq1_residual(gpu_lib, full):
     del off, idx, coff, cidx
 
     # Eq. 1 on the final ranks, with rows and out-degrees from the oracle
-    resid = full["resid"]
-    rin = oracle.sample_rows(n, src, dst, resid, "in", batch=batch)
-    nbrs = np.unique(np.concatenate(rin)).astype(np.int32)
-    nbr_deg = np.array([len(r) for r in oracle.sample_rows(n, src, dst, nbrs, "out", batch=batch,
-                                                           cap=1 << 26)], np.float64)
+    resid, rin, nbrs, nbr_deg = eq1_inputs(full)
     for v, row in zip(resid, rin):
         d = nbr_deg[np.searchsorted(nbrs, row)]
         r = (1.0 - ALPHA) / n + ALPHA * float(np.sum(R[row] / d))
@@ -82,3 +92,27 @@ def test_full_size_rows_and_eq1_residual(gpu_lib, full):
         bound = ALPHA * 2.0 * DRIFT * TOL_F * float(np.sum(1.0 / d)) + TOL / 1000 + 1e-14
         assert abs(r - R[v]) <= bound, (int(v), abs(r - R[v]), bound)
     assert np.all(R > 0)
+
+
+def test_full_size_fp32_eq1_residual(gpu_lib, full):
+    """FP32 ranks with compensated sums and per-vertex relative tolerances
+    (tol = 1e-7), as the benchmark's FP32 line runs them. If every rank is
+    within a relative E of the fixed point, the Eq. 1 residual of v is at
+    most 2 E R[v]: the in-sum carries at most E (R[v] - (1 - a)/n), the
+    vertex's own rank E R[v]. The FP32 accuracy target is E = 1e-6."""
+    n, src, dst, batch = full["n"], full["src"], full["dst"], full["batch"]
+    g = gpu_lib.graph_load(n, src, dst, gpu_lib.default_config(precision=gpu_lib.FP32))
+    st0 = g.static_pagerank(gpu_lib.default_params(mode=gpu_lib.JACOBI, tol=1e-10, max_iter=1000))
+    assert st0.status == gpu_lib.OK
+    g.apply_batch(*batch)
+    st = g.df_pagerank(gpu_lib.default_params(tol=1e-7))
+    assert st.status == gpu_lib.OK
+    R = g.get_ranks()
+    assert np.all(R > 0)
+    resid, rin, nbrs, nbr_deg = eq1_inputs(full)
+    worst = 0.0
+    for v, row in zip(resid, rin):
+        d = nbr_deg[np.searchsorted(nbrs, row)]
+        r = (1.0 - ALPHA) / n + ALPHA * float(np.sum(R[row] / d))
+        worst = max(worst, abs(r - R[v]) / R[v])
+    assert worst <= 2e-6, worst
