@@ -468,6 +468,30 @@ def pct(xs, q):
     return float(np.percentile(np.asarray(xs, np.float64), q)) if len(xs) else None
 
 
+def assign_by_edges(edges, ws):
+    """Graphs of a set assigned to ws ranks: largest first, each to the rank
+    with the fewest edges so far, since an update's work grows with the
+    graph's edges. Returns one sorted list of graph indices per rank."""
+    load = [0] * ws
+    out = [[] for _ in range(ws)]
+    for i in sorted(range(len(edges)), key=lambda i: (-edges[i], i)):
+        r = min(range(ws), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += edges[i]
+    return [sorted(x) for x in out]
+
+
+def gather_to_rank0(xs):
+    """Every rank's list, concatenated in rank order (xs itself without a
+    process group). All ranks call it; only rank 0 needs the result."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(xs)
+    got = [None] * dist.get_world_size()
+    dist.all_gather_object(got, list(xs))
+    return [x for part in got for x in part]
+
+
 def run_many(args):
     """Many graphs in one persistent launch per step (a set loaded with
     dfpr_graph_load_parts) against plain per-graph DF, one graph after another,
@@ -476,14 +500,24 @@ def run_many(args):
     import torch
 
     import paper_2407_19562_gb300 as dfpr
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     specs = workloads.many_graph_specs(args.graphs, 1000)
+    # the graphs shard across ranks with no collective on the data path
+    mine = assign_by_edges([int(round(n * deg)) for n, deg, _ in specs], ws)[rank]
     graphs, off = [], [0]
-    for i, (n, deg, frac) in enumerate(specs):
+    for i in mine:
+        n, deg, frac = specs[i]
         n, src, dst = workloads.rmat_graph_n(n, deg, 1000 + i)
-        graphs.append((n, src, dst, frac))
+        graphs.append((n, src, dst, frac, i))
         off.append(off[-1] + n)
     off = np.array(off, np.int64)
     gsrc = np.concatenate([g[1] + o for g, o in zip(graphs, off)]).astype(np.int32)
@@ -495,7 +529,7 @@ def run_many(args):
     st0 = dfpr.static_pagerank(s_set, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
     R0 = dfpr.get_ranks(s_set)
     singles = []
-    for i, (n, src, dst, frac) in enumerate(graphs):
+    for i, (n, src, dst, frac, _) in enumerate(graphs):
         g = dfpr.graph_load(n, src, dst, cfg, stream=stream.cuda_stream)
         dfpr.set_ranks(g, np.ascontiguousarray(R0[off[i]:off[i + 1]]))
         singles.append(g)
@@ -507,17 +541,17 @@ def run_many(args):
 
     def batches_for(step):
         out = []
-        for i, (n, src, dst, frac) in enumerate(graphs):
+        for n, src, dst, frac, gi in graphs:
             b = max(1, int(round(frac * len(src))))
-            out.append(workloads.uniform_batch(n, b, 7000 + 1000 * step + i, src, dst))
+            out.append(workloads.uniform_batch(n, b, 7000 + 1000 * step + gi, src, dst))
         return out
 
     set_lat, single_lat, set_step, single_step, set_kernel = [], [], [], [], []
     for step in range(total):
         bl = batches_for(step)
         gb = [np.concatenate([b[k] + o for b, o in zip(bl, off)]).astype(np.int32) for k in range(4)]
-        dev_gb = [torch.from_numpy(x).cuda() for x in gb]
-        dev_bl = [[torch.from_numpy(x).cuda() for x in b] for b in bl]
+        dev_gb = [torch.from_numpy(x).to(dev) for x in gb]
+        dev_bl = [[torch.from_numpy(x).to(dev) for x in b] for b in bl]
         torch.cuda.synchronize()
         # the set: one apply + one persistent launch for every graph
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -556,18 +590,31 @@ def run_many(args):
     Rs = dfpr.get_ranks(s_set)
     diff = max(float(np.max(np.abs(Rs[off[i]:off[i + 1]] - dfpr.get_ranks(g))))
                for i, g in enumerate(singles))
+    # whole job: every rank's graphs, timed by the slowest rank
+    diff = max_over_ranks(diff, dev)
+    set_total = max_over_ranks(float(np.sum(set_step)), dev)
+    single_total = max_over_ranks(float(np.sum(single_step)), dev)
+    kernel_total = max_over_ranks(float(np.sum(set_kernel)), dev)
+    set_lat, single_lat = gather_to_rank0(set_lat), gather_to_rank0(single_lat)
+    m_total = gather_to_rank0([int(len(gsrc))])
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
     line = {
         "metric": "many-graph DF: ms/step and per-graph p50/p99 latency (batched vs per-graph)",
-        "value": float(np.mean(set_step)), "unit": "ms/step", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "higher_is_better": False, "dtype": "f64" if prec == dfpr.FP64 else "f32",
+        "value": set_total / args.steps, "unit": "ms/step", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "scaling": "strong",
+        "dtype": "f64" if prec == dfpr.FP64 else "f32",
         "data": "synthetic",
         "config": {"workload": f"many{args.graphs}: R-MAT n log-uniform [1e3,1e6], avg degree U[4,32], "
                                "batches 0.1-1% of each graph's edges (80/20)",
-                   "graphs": args.graphs, "n_total": int(off[-1]), "m_raw_total": int(len(gsrc)),
+                   "graphs": args.graphs, "n_total": int(sum(n for n, _, _ in specs)),
+                   "m_raw_total": int(sum(m_total)), "m_raw_per_rank": m_total,
+                   "sharding": "graphs to ranks by greedy balance of edge draws, no collective",
                    "precision": args.precision},
-        "batched": {"ms_per_step": float(np.mean(set_step)), "kernel_ms": float(np.mean(set_kernel)),
+        "batched": {"ms_per_step": set_total / args.steps, "kernel_ms": kernel_total / args.steps,
                     "p50_ms": pct(set_lat, 50), "p99_ms": pct(set_lat, 99)},
-        "per_graph_sequential": {"ms_per_step": float(np.mean(single_step)),
+        "per_graph_sequential": {"ms_per_step": single_total / args.steps,
                                  "p50_ms": pct(single_lat, 50), "p99_ms": pct(single_lat, 99)},
         "max_abs_diff_batched_vs_alone": diff,
         "splits": {"gather_split": int(params.gather_split), "mark_split": int(params.mark_split),
@@ -575,6 +622,8 @@ def run_many(args):
                    "trial_ms": [float(x) for x in tune_trials] if args.autotune else None},
     }
     print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_serve(args):

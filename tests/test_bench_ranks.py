@@ -1,6 +1,7 @@
 """The multi-rank path of bench.py on the CPU: two gloo ranks, 127.0.0.1
-rendezvous. The timing aggregate is the slowest rank's total, and under
-torchrun the reference arm prints one line, from rank 0 only."""
+rendezvous. The timing aggregate is the slowest rank's total, under torchrun
+the reference arm prints one line, from rank 0 only, and a graph set shards
+over ranks by edges, with per-graph results gathered on rank 0."""
 import importlib.util
 import json
 import os
@@ -8,6 +9,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -65,3 +67,39 @@ def test_reference_arm_prints_once_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_graph_set_assignment_covers_and_balances():
+    bench = load_bench()
+    rng = np.random.default_rng(3)
+    edges = [int(x) for x in rng.integers(1_000, 1_000_000, 256)]
+    for ws in (1, 2, 3, 8):
+        parts = bench.assign_by_edges(edges, ws)
+        assert len(parts) == ws
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(edges)))          # each graph exactly once
+        loads = [sum(edges[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(edges)    # greedy, largest first
+        assert bench.assign_by_edges(edges, ws) == parts  # deterministic
+    assert bench.assign_by_edges([5, 3], 4) == [[0], [1], [], []]
+
+
+def _gather_main(rank, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    bench = load_bench()
+    mine = [[1.5, 2.5], [7.0]][rank]                 # per-graph latencies of this rank
+    out[rank] = bench.gather_to_rank0(mine)
+    dist.destroy_process_group()
+
+
+def test_per_graph_results_gathered_over_two_gloo_ranks():
+    port = free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_gather_main, args=(port, out), nprocs=2, join=True)
+        got = dict(out)
+    assert got[0] == [1.5, 2.5, 7.0]
+    bench = load_bench()
+    assert bench.gather_to_rank0([4.0]) == [4.0]        # no process group: itself
