@@ -638,11 +638,23 @@ def run_serve(args):
     import torch
 
     import paper_2407_19562_gb300 as dfpr
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
     scales = [18, 18, 19, 19, 20, 20, 21, 22]
+    # the resident graphs shard across ranks; each rank serves the requests
+    # to its own graphs, at the same fraction of its own measured capacity
+    if ws > len(scales):
+        raise SystemExit(f"serve8 shards {len(scales)} graphs: use at most {len(scales)} ranks")
+    mine = assign_by_edges([16 << sc for sc in scales], ws)[rank]
+    local_of = {gi: k for k, gi in enumerate(mine)}
     graphs, off = [], [0]
-    for i, sc in enumerate(scales):
-        n, src, dst = workloads.rmat_graph(sc, 16, 5000 + i)
+    for i in mine:
+        n, src, dst = workloads.rmat_graph(scales[i], 16, 5000 + i)
         graphs.append((n, src, dst))
         off.append(off[-1] + n)
     off = np.array(off, np.int64)
@@ -654,18 +666,24 @@ def run_serve(args):
     gset = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=None)
     st0 = dfpr.static_pagerank(gset, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
     params = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
-    u = workloads.uniform01(6000, 1, 3 * 7 * args.requests + 256)
+    u = workloads.uniform01(6000, 1, 3 * 7 * args.requests * ws + 256 * ws)
 
     def make_requests(k0, count):
+        """This rank's share of `count` requests of the global stream (graph
+        uniform over all resident graphs), with graph ids local to the rank."""
         reqs = []
         for j in range(count):
-            gi = int(u[k0 + 3 * j] * len(graphs)) % len(graphs)
+            gi = int(u[k0 + 3 * j] * len(scales)) % len(scales)
+            if gi not in local_of:
+                continue
             b = int(round(10.0 ** (1.0 + 4.0 * u[k0 + 3 * j + 1])))
-            n, src, dst = graphs[gi]
-            reqs.append((gi, workloads.uniform_batch(n, b, 60000 + k0 + j, src, dst)))
+            n, src, dst = graphs[local_of[gi]]
+            reqs.append((local_of[gi], workloads.uniform_batch(n, b, 60000 + k0 + j, src, dst)))
         return reqs
 
     def run_stream(reqs, gaps, slots):
+        if not reqs:
+            raise SystemExit("a rank drew no requests: raise --requests")
         srv = dfpr.server_create(gset, params, max_slots=slots, mem_fraction=0.5)
         ids = [None] * len(reqs)
         t0 = time.perf_counter()
@@ -687,14 +705,17 @@ def run_serve(args):
         lat = [i.done_ms - i.submit_ms for i in infos]
         span = (max(i.done_ms for i in infos) - min(i.submit_ms for i in infos)) / 1e3
         edges = sum(len(b[0]) + len(b[2]) for _, b in reqs)
+        # whole job: latencies of every rank, rates summed over ranks
+        lat = gather_to_rank0(lat)
+        tot = gather_to_rank0([(edges, len(reqs), span, len({i.cycle for i in infos}),
+                                sum(i.status != dfpr.OK for i in infos))])
         return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(np.mean(lat)),
-                "updates_per_s": edges / span if span > 0 else None,
-                "requests_per_s": len(reqs) / span if span > 0 else None,
-                "cycles": len({i.cycle for i in infos}),
-                "bad": sum(i.status != dfpr.OK for i in infos)}
+                "updates_per_s": sum(t[0] / t[2] for t in tot if t[2] > 0),
+                "requests_per_s": sum(t[1] / t[2] for t in tot if t[2] > 0),
+                "cycles": sum(t[3] for t in tot), "bad": sum(t[4] for t in tot)}
 
     # single-stream capacity: requests served one at a time, back to back
-    cal = make_requests(0, 40)
+    cal = make_requests(0, 40 * ws)
     srv = dfpr.server_create(gset, params, max_slots=1)
     svc = []
     for gi, batch in cal:
@@ -702,32 +723,38 @@ def run_serve(args):
         svc.append(r.done_ms - r.admit_ms)
     srv.destroy()
     mean_svc = float(np.mean(svc))
+    svc_all = gather_to_rank0([mean_svc])
     points = []
-    k = 200
+    k = max(200, 120 * ws + 8)  # past the calibration draws
     for load in (0.5, 0.8, 0.95):
         # fresh batches for each form (a replayed batch would be all no-ops),
         # same distribution and the same arrival times
-        reqs_b = make_requests(k, args.requests)
-        reqs_p = make_requests(k + 3 * args.requests, args.requests)
-        k += 6 * args.requests
+        reqs_b = make_requests(k, args.requests * ws)
+        reqs_p = make_requests(k + 3 * args.requests * ws, args.requests * ws)
+        k += 6 * args.requests * ws
         rate = load / (mean_svc / 1e3)
-        rng = np.random.default_rng(int(load * 100))
-        gaps = rng.exponential(1.0 / rate, size=args.requests)
+        rng = np.random.default_rng(int(load * 100) + 1000 * rank)
+        gaps = rng.exponential(1.0 / rate, size=len(reqs_b))
         batched = run_stream(reqs_b, gaps, 64)
-        plain = run_stream(reqs_p, gaps, 1)
+        plain = run_stream(reqs_p[:len(reqs_b)], gaps, 1)
         points.append({"load": load, "offered_req_per_s": rate, "batched": batched, "plain": plain})
     line = {
         "metric": "serving: per-batch p50/p99 latency (ms) and updates/s, batched vs one request per cycle",
         "value": points[-1]["batched"]["p99_ms"], "unit": "ms (p99 at 95% load, batched)",
-        "n_gpus": 1, "higher_is_better": False,
+        "n_gpus": ws, "higher_is_better": False, "scaling": "weak",
         "dtype": "f64" if prec == dfpr.FP64 else "f32", "data": "synthetic",
         "config": {"workload": "serve8: R-MAT scales 18,18,19,19,20,20,21,22; Poisson arrivals; "
                                "batch sizes log-uniform [10,1e5], 80/20",
-                   "requests_per_point": args.requests, "mean_service_ms": mean_svc,
+                   "requests_per_point": args.requests, "mean_service_ms": svc_all,
+                   "sharding": "graphs to ranks by greedy balance of edge draws; each rank "
+                               "at the load fraction of its own capacity",
                    "precision": args.precision},
         "points": points,
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_faults(args):
