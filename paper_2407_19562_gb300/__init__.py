@@ -14,7 +14,6 @@ ranks are valid but not converged.
 from __future__ import annotations
 
 import ctypes
-import os
 import threading
 
 import numpy as np
