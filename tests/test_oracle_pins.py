@@ -153,6 +153,32 @@ def test_reference_matches_dense_solve(seed):
     assert np.max(np.abs(R10 - exact)) < 1e-10 / (1 - ALPHA)
 
 
+@pytest.mark.parametrize("alpha", [0.5, 0.95])
+@pytest.mark.parametrize("seed", range(3))
+def test_other_damping_matches_dense_solve(seed, alpha):
+    """The oracle's Static_BB and DF_BB at damping factors other than 0.85,
+    which the GPU parity tests compare against."""
+    rng = np.random.default_rng(200 + seed)
+    n = int(rng.integers(2, 65))
+    src, dst = random_graph(n, rng.uniform(0.02, 0.3), rng)
+    g = oracle.Graph.build(n, src, dst, True)
+    exact = dense_pagerank(adjacency(n, src, dst), alpha=alpha)
+    R, _ = g.static_bb(alpha=alpha, tol=oracle.REF_TOL, max_iter=oracle.MAX_ITER)
+    assert np.max(np.abs(R - exact)) < 1e-13
+    # DF_BB after a batch of two insertions lands within the 1/(1 - alpha) bound
+    A = adjacency(n, src, dst)
+    ins = [(int(u), int(v)) for u, v in zip(*np.nonzero(~A))][:2]
+    e = np.zeros(0, np.int32)
+    batch = (e, e, np.array([u for u, _ in ins], np.int32), np.array([v for _, v in ins], np.int32))
+    g1, _ = g.apply(*batch)
+    R1, st = g1.df_bb(R, alpha=alpha)
+    A1 = A.copy()
+    for u, v in ins:
+        A1[u, v] = True
+    exact1 = dense_pagerank(A1, alpha=alpha)
+    assert np.max(np.abs(R1 - exact1)) < oracle.TOL / (1 - alpha)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_teleport_reading_matches_dense_solve(seed):
     rng = np.random.default_rng(100 + seed)
