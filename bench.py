@@ -137,7 +137,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 
 def algorithmic_bytes(st, s_r: int) -> float:
-    """Bytes the method must move for the counted work (see DESIGN.md):
+    """Bytes the method must move for the counted work:
     per recomputed vertex: in-row descriptor (16 B), own rank read, rank and
     contribution writes (3 s_R), out-row descriptor for its degree (16 B);
     per gathered in-edge: id (4 B) + contribution (s_R); per expansion: the
@@ -545,7 +545,7 @@ def run_many(args):
             out.append(workloads.uniform_batch(n, b, 7000 + 1000 * step + gi, src, dst))
         return out
 
-    set_lat, single_lat, set_step, single_step, set_kernel = [], [], [], [], []
+    set_lat, single_lat, set_step, single_step, set_kernel, set_bytes = [], [], [], [], [], []
     for step in range(total):
         bl = batches_for(step)
         gb = [np.concatenate([b[k] + o for b, o in zip(bl, off)]).astype(np.int32) for k in range(4)]
@@ -585,6 +585,7 @@ def run_many(args):
             set_step.append(step_ms)
             single_step.append(lat1[-1])
             set_kernel.append(st.ms)
+            set_bytes.append(algorithmic_bytes(st.as_dict(), 8 if prec == dfpr.FP64 else 4))
     # both forms reach the same ranks (each graph's update is the same method)
     Rs = dfpr.get_ranks(s_set)
     diff = max(float(np.max(np.abs(Rs[off[i]:off[i + 1]] - dfpr.get_ranks(g))))
@@ -594,6 +595,11 @@ def run_many(args):
     set_total = max_over_ranks(float(np.sum(set_step)), dev)
     single_total = max_over_ranks(float(np.sum(single_step)), dev)
     kernel_total = max_over_ranks(float(np.sum(set_kernel)), dev)
+    # roofline of the set's persistent kernel: algorithmic bytes of every
+    # rank over the slowest rank's kernel time
+    bytes_total = sum(gather_to_rank0([float(np.sum(set_bytes))]))
+    peak, peak_kind = load_peaks()
+    achieved = bytes_total / (kernel_total * 1e-3) / 1e9 if kernel_total > 0 else 0.0
     set_lat, single_lat = gather_to_rank0(set_lat), gather_to_rank0(single_lat)
     m_total = gather_to_rank0([int(len(gsrc))])
     if rank != 0:
@@ -616,6 +622,10 @@ def run_many(args):
         "per_graph_sequential": {"ms_per_step": single_total / args.steps,
                                  "p50_ms": pct(single_lat, 50), "p99_ms": pct(single_lat, 99)},
         "max_abs_diff_batched_vs_alone": diff,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_worklist over the set (one launch per step)",
+                     "algorithmic_bytes_per_launch": bytes_total / args.steps},
         "splits": {"gather_split": int(params.gather_split), "mark_split": int(params.mark_split),
                    "autotuned": bool(args.autotune),
                    "trial_ms": [float(x) for x in tune_trials] if args.autotune else None},
