@@ -221,10 +221,13 @@ dfpr_status dfpr_graph_parts(const dfpr_graph* g, int32_t* k);
  */
 dfpr_status dfpr_get_part_times(const dfpr_graph* g, double* ms);
 
-/* Releases every device and host resource of g (NULL is a no-op). */
+/* Releases every device and host resource of g (NULL is a no-op). Returns
+   EBUSY, and frees nothing, while another call on g is in progress. */
 dfpr_status dfpr_graph_free(dfpr_graph* g);
 
-/* Makes later calls on g issue their work on cuda_stream (a cudaStream_t). */
+/* Makes later calls on g issue their work on cuda_stream (a cudaStream_t; NULL:
+   a new stream of the library's). A stream the library created is kept until
+   dfpr_graph_free, since arrays allocated on it may name it when released. */
 dfpr_status dfpr_graph_set_stream(dfpr_graph* g, void* cuda_stream);
 
 /* n, current edge count m (self-loops included) and device id of g. */

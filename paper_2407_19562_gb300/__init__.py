@@ -253,9 +253,10 @@ class Graph:
         return self._h
 
     def free(self):
-        h, self._h = self._h, None
+        h = self._h
         if h:
-            _check(load().dfpr_graph_free(h), "graph_free")
+            _check(load().dfpr_graph_free(h), "graph_free")  # EBUSY keeps the handle
+            self._h = None
 
     def __del__(self):
         try:

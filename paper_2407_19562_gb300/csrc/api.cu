@@ -382,6 +382,11 @@ dfpr_status dfpr_get_part_times(const dfpr_graph* g, double* ms) {
 
 dfpr_status dfpr_graph_free(dfpr_graph* g) {
   if (!g) return DFPR_OK;
+  int idle = 0;
+  if (!g->busy.compare_exchange_strong(idle, 1)) {
+    set_error("dfpr_graph_free: another call on this graph is in progress");
+    return DFPR_EBUSY;
+  }
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != g->device) cudaSetDevice(g->device);
@@ -389,9 +394,14 @@ dfpr_status dfpr_graph_free(dfpr_graph* g) {
   cudaStream_t s = g->stream;
   const bool own = g->own_stream;
   unsigned long long* pinned = g->pinned;
-  delete g;  // device arrays are released by their destructors
+  std::vector<cudaStream_t> retired;
+  retired.swap(g->retired_streams);
+  // device arrays are released by their destructors, with the streams they
+  // were allocated on still alive (an installed allocator may use them)
+  delete g;
   if (pinned) cudaFreeHost(pinned);
   if (own && s) cudaStreamDestroy(s);
+  for (cudaStream_t r : retired) cudaStreamDestroy(r);
   if (prev >= 0) cudaSetDevice(prev);
   return DFPR_OK;
 }
@@ -406,7 +416,8 @@ dfpr_status dfpr_graph_set_stream(dfpr_graph* g, void* cuda_stream) {
   DeviceGuard dg(g->device);
   DFPR_CUDA(cudaStreamSynchronize(g->stream));
   if (g->own_stream) {
-    DFPR_CUDA(cudaStreamDestroy(g->stream));
+    // kept until the graph is freed: arrays allocated on it record it
+    g->retired_streams.push_back(g->stream);
     g->own_stream = false;
   }
   if (cuda_stream) {

@@ -269,6 +269,8 @@ struct dfpr_graph {
   dfpr::DevArray<unsigned long long> host_sync;  // small device words read back
   unsigned long long* pinned = nullptr;   // pinned host words for read-back
   std::atomic<int> busy{0};
+  std::vector<cudaStream_t> retired_streams;  // owned streams replaced by set_stream,
+                                              // destroyed with the graph
   int sm_count = 0;
   int max_ctas = 0;
 };
