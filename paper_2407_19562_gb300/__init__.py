@@ -39,6 +39,8 @@ _STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "EBU
 
 
 class DfprError(RuntimeError):
+    """A failed library call: .status is the dfpr_status code; the message is
+    the library's dfpr_last_error() text."""
     def __init__(self, status: int, where: str, message: str):
         name = _STATUS_NAMES[status] if 0 <= status < len(_STATUS_NAMES) else str(status)
         super().__init__(f"{where}: {name}: {message}")
@@ -46,12 +48,14 @@ class DfprError(RuntimeError):
 
 
 class Config(ctypes.Structure):
+    """dfpr_graph_config: options fixed when a graph is loaded."""
     _fields_ = [("precision", ctypes.c_int32), ("dead_end", ctypes.c_int32),
                 ("row_slack", ctypes.c_double), ("min_slack", ctypes.c_int32),
                 ("reorder", ctypes.c_int32), ("tail_slack", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
+    """dfpr_params: parameters of one rank computation (see default_params)."""
     _fields_ = [("alpha", ctypes.c_double), ("tol", ctypes.c_double),
                 ("frontier_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("normalize", ctypes.c_int32),
@@ -62,6 +66,7 @@ class Params(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
+    """dfpr_stats: counters of one call; .status holds the call's dfpr_status."""
     _fields_ = [("processed", ctypes.c_int64), ("edges_gathered", ctypes.c_int64),
                 ("expansions", ctypes.c_int64), ("edges_marked", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("affected", ctypes.c_int64),
@@ -80,6 +85,7 @@ class Stats(ctypes.Structure):
 
 
 class RequestInfo(ctypes.Structure):
+    """dfpr_request_info: outcome and host-clock times of one served request."""
     _fields_ = [("status", ctypes.c_int32), ("cycle_requests", ctypes.c_int32),
                 ("cycle", ctypes.c_int64), ("submit_ms", ctypes.c_double),
                 ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
@@ -153,6 +159,7 @@ def load():
 
 
 def version() -> int:
+    """dfpr_version: the library's ABI version."""
     return int(load().dfpr_version())
 
 
@@ -162,6 +169,7 @@ def kernel_launches() -> int:
 
 
 def last_error() -> str:
+    """dfpr_last_error: this thread's last error message."""
     return (load().dfpr_last_error() or b"").decode(errors="replace")
 
 
@@ -171,6 +179,7 @@ def _check(rc: int, where: str):
 
 
 def default_config(**kw) -> Config:
+    """dfpr_default_config, with any field overridden by keyword."""
     c = Config()
     load().dfpr_default_config(ctypes.byref(c))
     for k, v in kw.items():
@@ -179,6 +188,8 @@ def default_config(**kw) -> Config:
 
 
 def default_params(**kw) -> Params:
+    """dfpr_default_params (the paper's constants), with any field overridden by
+    keyword."""
     p = Params()
     load().dfpr_default_params(ctypes.byref(p))
     for k, v in kw.items():
@@ -347,14 +358,18 @@ def get_part_times(g: Graph) -> np.ndarray:
 
 
 def graph_free(g: Graph):
+    """dfpr_graph_free (EBUSY while another call on g runs)."""
     g.free()
 
 
 def graph_set_stream(g: Graph, stream):
+    """dfpr_graph_set_stream: later calls on g run on `stream` (a cudaStream_t;
+    None: a new stream of the library's)."""
     _check(load().dfpr_graph_set_stream(g.handle, stream), "graph_set_stream")
 
 
 def graph_info(g: Graph):
+    """dfpr_graph_info -> {"n", "m" (edges with self-loops), "device"}."""
     n, m, dev = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
     _check(load().dfpr_graph_info(g.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(dev)),
            "graph_info")
@@ -385,6 +400,9 @@ def _run(fn, where, g, params):
 
 
 def df_pagerank(g: Graph, params: Params | None = None) -> Stats:
+    """dfpr_df_pagerank: the DF update for the pending changes. ENOTCONV and
+    ETIMEOUT come back in Stats.status (ranks valid, not converged); other
+    failures raise DfprError."""
     return _run(load().dfpr_df_pagerank, "df_pagerank", g, params)
 
 
@@ -410,10 +428,12 @@ def autotune(g: Graph, params: Params | None = None, candidates=None):
 
 
 def nd_pagerank(g: Graph, params: Params | None = None) -> Stats:
+    """dfpr_nd_pagerank: naive-dynamic update from the current ranks."""
     return _run(load().dfpr_nd_pagerank, "nd_pagerank", g, params)
 
 
 def static_pagerank(g: Graph, params: Params | None = None) -> Stats:
+    """dfpr_static_pagerank: ranks from 1/n on the current graph."""
     return _run(load().dfpr_static_pagerank, "static_pagerank", g, params)
 
 
@@ -428,6 +448,8 @@ def get_ranks(g: Graph, out=None):
 
 
 def set_ranks(g: Graph, ranks):
+    """dfpr_set_ranks from a float64 array (numpy, or torch on the host or the
+    graph's device)."""
     p, _, dev = _ptr(ranks, np.float64, g.n, "ranks")
     _check(load().dfpr_set_ranks(g.handle, p, dev), "set_ranks")
 
@@ -448,10 +470,13 @@ def _export(fn, where, g, offsets, idx):
 
 
 def get_csr(g: Graph, offsets=None, idx=None):
+    """dfpr_get_csr -> (offsets int64[n + 1], idx int32[m]), caller ids; writes
+    into the given arrays (host or device) when passed."""
     return _export(load().dfpr_get_csr, "get_csr", g, offsets, idx)
 
 
 def get_csc(g: Graph, offsets=None, idx=None):
+    """dfpr_get_csc -> (offsets int64[n + 1], idx int32[m]), caller ids."""
     return _export(load().dfpr_get_csc, "get_csc", g, offsets, idx)
 
 
@@ -475,6 +500,7 @@ class Server:
         self.graph = graph
 
     def submit(self, part, del_src, del_dst, ins_src, ins_dst) -> int:
+        """dfpr_server_submit: queues one batch for graph `part` -> request id."""
         a = [np.ascontiguousarray(x, np.int32) for x in (del_src, del_dst, ins_src, ins_dst)]
         if len(a[0]) != len(a[1]) or len(a[2]) != len(a[3]):
             raise DfprError(EINVAL, "server_submit", "source and target lengths differ")
@@ -485,14 +511,18 @@ class Server:
         return int(rid.value)
 
     def wait(self, request_id: int) -> RequestInfo:
+        """dfpr_server_wait: blocks until the request's cycle finished."""
         info = RequestInfo()
         _check(load().dfpr_server_wait(self._h, int(request_id), ctypes.byref(info)), "server_wait")
         return info
 
     def drain(self):
+        """dfpr_server_drain: blocks until every queued request is served."""
         _check(load().dfpr_server_drain(self._h), "server_drain")
 
     def destroy(self):
+        """dfpr_server_destroy: drains, stops the thread and frees the server (the
+        graph stays)."""
         h, self._h = self._h, None
         if h:
             _check(load().dfpr_server_destroy(h), "server_destroy")
@@ -506,6 +536,9 @@ class Server:
 
 def server_create(g: Graph, params: Params | None = None, max_slots: int = 64,
                   mem_fraction: float = 0.5) -> Server:
+    """dfpr_server_create: starts a server thread on g; a cycle admits up to
+    max_slots queued requests while their batches fit mem_fraction of the
+    device's free memory, and updates them in one launch."""
     h = ctypes.c_void_p()
     _check(load().dfpr_server_create(g.handle, ctypes.byref(params) if params is not None else None,
                                      int(max_slots), float(mem_fraction), ctypes.byref(h)),
