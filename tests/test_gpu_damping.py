@@ -21,6 +21,11 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
 MODES = ["WORKLIST", "ROUND", "JACOBI"]
+# The paper's MAX_ITERATIONS = 500 is set for alpha = 0.85. An iteration
+# shrinks the error by about alpha, so alpha = 0.95 needs about
+# log(0.85) / log(0.95) = 3.2 times the passes. The round schedule's
+# lock-free passes came within reach of 500 there, so the cap is scaled.
+MAX_ITER = 2000
 
 
 def bound(alpha):
@@ -44,7 +49,7 @@ def case(request):
 def test_static_at_other_damping(gpu_lib, case, mode):
     g = gpu_lib.graph_load(case["n"], case["src"], case["dst"])
     st = g.static_pagerank(gpu_lib.default_params(mode=getattr(gpu_lib, mode), alpha=case["alpha"],
-                                                  tol=TOL, max_iter=1000))
+                                                  tol=TOL, max_iter=MAX_ITER))
     assert st.status == gpu_lib.OK
     err = np.max(np.abs(g.get_ranks() - case["ref0"]))
     assert err <= bound(case["alpha"]), err
@@ -56,8 +61,8 @@ def test_df_at_other_damping(gpu_lib, case, mode):
     g.set_ranks(case["ref0"])
     assert g.apply_batch(*case["batch"]) == case["nreal"]
     st = g.df_pagerank(gpu_lib.default_params(mode=getattr(gpu_lib, mode), alpha=case["alpha"],
-                                              tol=TOL))
-    assert st.status == gpu_lib.OK
+                                              tol=TOL, max_iter=MAX_ITER))
+    assert st.status == gpu_lib.OK, st.as_dict()
     err = np.max(np.abs(g.get_ranks() - case["ref1"]))
     assert err <= bound(case["alpha"]), err
 
@@ -66,8 +71,9 @@ def test_jacobi_df_follows_oracle_df_bb(gpu_lib, case):
     g = gpu_lib.graph_load(case["n"], case["src"], case["dst"])
     g.set_ranks(case["ref0"])
     g.apply_batch(*case["batch"])
-    st = g.df_pagerank(gpu_lib.default_params(mode=gpu_lib.JACOBI, alpha=case["alpha"], tol=TOL))
-    R_o, st_o = case["g1"].df_bb(case["ref0"], alpha=case["alpha"], tol=TOL)
+    st = g.df_pagerank(gpu_lib.default_params(mode=gpu_lib.JACOBI, alpha=case["alpha"], tol=TOL,
+                                              max_iter=MAX_ITER))
+    R_o, st_o = case["g1"].df_bb(case["ref0"], alpha=case["alpha"], tol=TOL, max_iter=MAX_ITER)
     assert st.passes == st_o.iterations
     assert st.affected == st_o.affected
     assert np.max(np.abs(g.get_ranks() - R_o)) <= 1e-12
