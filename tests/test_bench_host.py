@@ -55,3 +55,14 @@ def test_traffic_figure_retires_with_the_kernel_code(monkeypatch):
     monkeypatch.setattr(b, "kernel_source_hash", lambda: "0" * 16)
     assert b.measured_traffic(*key) is None     # changed code: no stale figure
     assert b.measured_traffic("rmat20-batch0.0001", "fp64", "worklist") is None
+
+
+def test_working_set_and_l2_flag():
+    import torch
+    b = load_bench()
+    # R-MAT scale 14 (the small workload) sits far inside a 126 MB L2; scale 24 does not
+    assert b.working_set_bytes(16384, 278_000, 8) < 4e6
+    assert b.working_set_bytes(16_777_216, 280_209_127, 8) > 3e9
+    assert b.working_set_bytes(10, 100, 4) == 8 * 100 + 10 * (32 + 16) + 10 // 4
+    if not torch.cuda.is_available():
+        assert b.l2_bytes(0) == 0       # unknown without a GPU, never an exception
