@@ -34,6 +34,10 @@ MUTATIONS = {
                                                  "    if (0) {"),
     "teleport_df_drops_dead_end_term": ("      double r = rank_of(gt, R, v, alpha, D, 1, &s);",
                                         "      double r = rank_of(gt, R, v, alpha, 0.0, 1, &s);"),
+    "df_lf_expansion_leaves_flags_clear": ("          VA[gt->out_idx[e]] = 1;\n          RC[gt->out_idx[e]] = 1;",
+                                           "          VA[gt->out_idx[e]] = 1;"),
+    "df_lf_initial_marking_leaves_flags_clear": ("  mark_initial(gt, VA, RC, C);",
+                                                 "  mark_initial(gt, VA, NULL, C);"),
 }
 
 

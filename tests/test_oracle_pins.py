@@ -495,3 +495,70 @@ def test_df_respects_max_iterations():
     assert st.iterations == 2 and not st.converged
     R, st = g1.df_bb(R0, max_iter=3)
     assert st.iterations == 3 and not st.converged
+
+
+# --------------------------------------------------------------------------
+# DF_LF's not-converged flags (Alg. 2, Sec. 4.3), derived by hand
+# --------------------------------------------------------------------------
+
+def test_df_lf_flags_keep_a_changed_source_for_one_more_pass():
+    # G^0: 1 -> 0 (no self-loops), n = 3; the batch inserts 2 -> 0, so the
+    # initial affected set is out(2) = {0}, flagged not converged (R_C = 1).
+    # Pass 1 recomputes 0: its rank moves by alpha*b > tau (b = (1-alpha)/n),
+    # so R_C[0] stays 1; 0 has no out-edges, so nothing else is marked.
+    # Pass 2 recomputes 0 from unchanged inputs: the change is exactly 0, so
+    # R_C[0] is cleared and the update stops. 2 passes, 2 recomputations of a
+    # vertex with 2 in-edges; ranks follow Eq. 1 in closed form.
+    n = 3
+    b = (1.0 - ALPHA) / n
+    g0 = oracle.Graph.build(n, [1], [0], self_loops=False)
+    R0 = np.array([b * (1 + ALPHA), b, b])
+    g1, nreal = g0.apply([], [], [2], [0])
+    assert nreal == (0, 1)
+    R, st = g1.df_lf(R0)
+    assert st.converged
+    assert st.iterations == 2
+    assert st.processed == 2 and st.edges == 4
+    assert st.affected == 1
+    assert np.max(np.abs(R - np.array([b * (1 + 2 * ALPHA), b, b]))) < 1e-16
+
+
+def test_df_lf_flags_follow_a_descending_chain():
+    # G^0: 3 -> 2 -> 1 -> 0 (no self-loops), n = 5; the batch inserts 4 -> 3.
+    # Ascending order visits a vertex before its in-neighbour on this chain, so
+    # the change reaches one vertex further per pass:
+    #   pass 1: {3} moves (alpha*b); marks 2 (VA = R_C = 1)
+    #   pass 2: {2, 3}: 2 moves (alpha^2 b), marks 1; 3 does not move, clears
+    #   pass 3: {1, 2, 3}: 1 moves, marks 0; 2 clears
+    #   pass 4: {0, 1, 2, 3}: 0 moves (no out-edges); 1 clears
+    #   pass 5: nothing moves; 0 clears; all flags clear -> stop.
+    # 5 passes, 1+2+3+4+4 = 14 recomputations of in-degree-1 vertices, and
+    # the exact ranks b * (1 + alpha + ... + alpha^k) along the chain.
+    n = 5
+    b = (1.0 - ALPHA) / n
+    g0 = oracle.Graph.build(n, [3, 2, 1], [2, 1, 0], self_loops=False)
+    geo = [sum(ALPHA ** j for j in range(k + 1)) for k in range(5)]
+    R0 = b * np.array([geo[3], geo[2], geo[1], geo[0], geo[0]])
+    g1, _ = g0.apply([], [], [4], [3])
+    R, st = g1.df_lf(R0)
+    assert st.converged
+    assert st.iterations == 5
+    assert st.processed == 14 and st.edges == 14
+    assert st.affected == 4
+    exact = b * np.array([geo[4], geo[3], geo[2], geo[1], geo[0]])
+    assert np.max(np.abs(R - exact)) < 1e-16
+
+
+def test_df_lf_tight_tolerance_matches_dense_solve():
+    # With tau = 1e-14 the fixed point is reached to within a few 1e-14 per
+    # vertex (error <= tau * (1 + alpha) / (1 - alpha) for a converged state),
+    # so a pass that stops while a vertex still moves shows up here.
+    n, g0, g1, R0, _ = rmat_case(scale=9, b=200, seed=21)
+    off, idx = g1.csr()
+    A = np.zeros((n, n), bool)
+    A[np.repeat(np.arange(n), np.diff(off)), idx] = True
+    exact = dense_pagerank(A)
+    R_ref0, _ = g0.reference()          # R^{t-1} at FP64 rounding, not at tau
+    R, st = g1.df_lf(R_ref0, tol=1e-14)
+    assert st.converged
+    assert np.max(np.abs(R - exact)) < 1e-12
