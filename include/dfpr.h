@@ -163,7 +163,9 @@ typedef struct dfpr_stats {
   int64_t affected;       /* distinct vertices recomputed at least once */
   int32_t passes;         /* iterations (jacobi) or passes (round); 0 for worklist */
   int32_t status;         /* dfpr_status of the call */
-  double residual_linf;   /* jacobi: last L-inf iterate difference; else max last change */
+  double residual_linf;   /* jacobi: last L-inf iterate difference; worklist and round:
+                             the largest change of one recomputation in the call (not a
+                             residual; dfpr_residual gives max_v |Eq. 1 (v) - R[v]|) */
   double rank_sum;        /* FP64 sum of the ranks after the call when normalize = 1,
                              else NaN */
   double ms;              /* device time (CUDA events): the persistent kernel alone in
@@ -327,31 +329,50 @@ dfpr_status dfpr_initial_affected(dfpr_graph* g, uint8_t* affected, int on_devic
                                   int64_t* count);
 
 /*
- * Serving: a server thread keeps a graph (usually a set from
- * dfpr_graph_load_parts) resident and serves update requests: each request is
- * one batch of edge deletions and insertions for one graph of the set. The
- * thread runs cycles: it admits queued requests in arrival order while a slot
- * is free (at most max_slots per cycle) and the cycle's batch memory fits in
- * mem_fraction of the device's free memory (a cycle always admits at least one
- * request), applies them (requests for the same graph in arrival order), then
- * updates every affected graph with one dfpr_df_pagerank call, i.e. one
- * persistent launch for all admitted requests. Requests that arrive during a
- * cycle join the next one: a batch may not change a graph while an update
- * reads it (read-only snapshot, Sec. 3.4). While the server exists, other
- * calls on its graph return DFPR_EBUSY; dfpr_server_drain waits until it is
- * idle. Times are host monotonic-clock ms since the server was created.
+ * Serving with continuous batching. A server keeps one or more units resident
+ * (a unit is a graph, or a set of graphs from dfpr_graph_load_parts) and
+ * serves update requests: each request is one batch of edge deletions and
+ * insertions for one graph. Every unit has its own worker thread and uses its
+ * own stream (load the units with distinct streams, e.g. cuda_stream NULL, for
+ * their launches to overlap). A unit's worker admits the unit's queued
+ * requests in arrival order whenever the unit is idle, a slot is free (at most
+ * max_slots requests are in flight over the whole server) and their batch
+ * memory fits in mem_fraction of the device's free memory minus what earlier
+ * admissions hold (with nothing else in flight one request is always
+ * admitted); it applies them (requests for the same graph in arrival order)
+ * and updates the unit with one dfpr_df_pagerank call, i.e. one persistent
+ * launch for all admitted requests of the unit. So a request for an idle unit
+ * starts at once, even while other units' updates run on the GPU, and their
+ * work overlaps on the device. A unit never changes while its own update
+ * reads it (read-only snapshot, Sec. 3.4): requests arriving for a busy unit
+ * join its next update. While the server exists, other calls on its units
+ * return DFPR_EBUSY; dfpr_server_drain waits until it is idle. Times are host
+ * monotonic-clock ms since the server was created.
  */
 typedef struct dfpr_server dfpr_server;
 
 typedef struct dfpr_request_info {
-  int32_t status;         /* dfpr_status of the request's cycle */
-  int32_t cycle_requests; /* requests served by the same cycle */
-  int64_t cycle;          /* index of that cycle */
+  int32_t status;         /* dfpr_status of the update that served it */
+  int32_t cycle_requests; /* requests served by the same update */
+  int64_t cycle;          /* index of that update (numbered over the server) */
   double submit_ms;       /* when dfpr_server_submit queued it */
-  double admit_ms;        /* when its cycle started */
-  double done_ms;         /* when its cycle's update finished */
+  double admit_ms;        /* when it was admitted (its update started) */
+  double done_ms;         /* when its update finished */
 } dfpr_request_info;
 
+/* A server over k units (graphs or sets, distinct). Parts are numbered over
+ * the units in order: unit 0's graphs first. grid_share > 0 caps every
+ * launch at that many CTAs (when params->grid_ctas is 0), so that updates of
+ * several units can be resident on the GPU together; 0 gives each launch a
+ * full grid. EINVAL (k < 1, a NULL or repeated unit, max_slots < 1,
+ * mem_fraction outside (0, 1], grid_share < 0), EBUSY (a unit is in use),
+ * ENOMEM. */
+dfpr_status dfpr_server_create_units(int32_t k, dfpr_graph* const* units, const dfpr_params* p,
+                                     int32_t max_slots, double mem_fraction, int32_t grid_share,
+                                     dfpr_server** out);
+
+/* A server over one unit (dfpr_server_create_units with k = 1, grid_share 0):
+ * every update of that unit batches all of its admitted requests. */
 dfpr_status dfpr_server_create(dfpr_graph* g, const dfpr_params* p, int32_t max_slots,
                                double mem_fraction, dfpr_server** out);
 
@@ -369,7 +390,7 @@ dfpr_status dfpr_server_wait(dfpr_server* s, int64_t request_id, dfpr_request_in
 /* Blocks until every queued request is done and the server is idle. */
 dfpr_status dfpr_server_drain(dfpr_server* s);
 
-/* Drains, stops the thread and frees the server (the graph stays). */
+/* Drains, stops the worker threads and frees the server (the units stay). */
 dfpr_status dfpr_server_destroy(dfpr_server* s);
 
 /*
@@ -386,14 +407,31 @@ dfpr_status dfpr_set_allocator(dfpr_alloc_fn alloc, dfpr_free_fn free_fn, void* 
 const char* dfpr_last_error(void);
 
 /*
- * Static PageRank (every rank starts at 1/n, Jacobi iteration of Eq. 1 until
- * the largest change is <= tol or max_iter iterations) over a graph the caller
- * already holds on the device, without allocating any device memory. The
- * paper has no counterpart: this entry point exists for callers that cannot
- * call cudaMalloc / cudaFree, for example code working inside a memory budget
- * that another component (a framework's pool allocator, a server's fixed
- * arena) owns entirely, or code that must not trigger the device-wide
- * synchronisation those calls imply.
+ * FP64 residual of the stored ranks (the L-inf test of Alg. 1, taken on the
+ * final state rather than on consecutive iterates): for every vertex,
+ * r'(v) = (1 - alpha)/n + alpha * sum over in-edges (u, v) of R[u] / |out(u)|
+ * (Eq. 1, Sec. 3.1; plus alpha * D / n under DFPR_TELEPORT, D the rank held
+ * by dead ends; n of the vertex's own graph in a set), summed in FP64 from the
+ * ranks themselves, not from the stored contributions. *linf receives
+ * max_v |r'(v) - R[v]|; *linf_rel (may be NULL) max_v |r'(v) - R[v]| / R[v].
+ * One sweep over every in-edge on the graph's stream; the ranks are not
+ * changed. Errors: EINVAL (NULL graph or linf, alpha outside (0, 1)), EBUSY,
+ * ECUDA.
+ */
+dfpr_status dfpr_residual(const dfpr_graph* g, double alpha, double* linf, double* linf_rel);
+
+/*
+ * Static PageRank over a graph the caller already holds on the device,
+ * without allocating any device memory: every rank starts at 1/n and each
+ * iteration recomputes all of them from the previous iterate,
+ * r_v = (1 - alpha)/n + alpha * (sum over in-edges (u, v) of r_u / d_out(u)
+ * + D/n), where D is the rank held by vertices without out-edges (0 when
+ * every vertex has one, e.g. a self-loop), until the largest change is
+ * <= tol or max_iter iterations have run. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc / cudaFree, for
+ * example code working inside a memory budget that another component (a
+ * framework's pool allocator, a server's fixed arena) owns entirely, or code
+ * that must not trigger the device-wide synchronisation those calls imply.
  *
  * Arguments (all arrays are device pointers on the current device):
  *   n           vertices, 1 <= n <= 1,048,576 (larger n returns EINVAL)
@@ -402,13 +440,14 @@ const char* dfpr_last_error(void);
  *   ranks       double[n], output
  *   iterations  host int32 (may be NULL): iterations performed
  *   cuda_stream the cudaStream_t to run on (NULL: the legacy default stream)
- * Scratch (a second rank vector, two contribution vectors and a reduction
- * word) lives in one fixed __device__ array of 24 MiB + 256 bytes that every
+ * Scratch (a second rank vector, two contribution vectors and three control
+ * words) lives in one fixed __device__ array of 24 MiB + 256 bytes that every
  * GPU loading this library keeps until the process exits. The first call on a
  * device looks up that array's device address (with the device current), so
- * make the first call before any stream capture. All calls share the array:
- * calls that overlap on the GPU race and give wrong results. Returns OK,
- * ENOTCONV (cap reached; ranks are the last iterate), EINVAL, ECUDA.
+ * make the first call before any stream capture; a cudaDeviceReset after it
+ * invalidates the address. All calls share the array: calls that overlap on
+ * the GPU race and give wrong results. Returns OK, ENOTCONV (cap reached;
+ * ranks are the last iterate), EINVAL, ECUDA.
  */
 dfpr_status dfpr_static_pagerank_noalloc(int32_t n, const int64_t* in_offsets,
                                          const int32_t* in_idx, const int32_t* out_degree,

@@ -25,7 +25,7 @@ __all__ = [
     "kernel_launches",
     "default_config", "default_params", "graph_load", "graph_free", "graph_info",
     "graph_set_stream", "apply_batch", "df_pagerank", "nd_pagerank", "static_pagerank",
-    "get_ranks", "set_ranks", "get_csr", "get_csc", "initial_affected", "set_allocator",
+    "get_ranks", "set_ranks", "residual", "get_csr", "get_csc", "initial_affected", "set_allocator",
     "graph_load_parts", "get_part_times", "Server", "RequestInfo", "server_create",
     "use_torch_allocator", "OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "EBUSY",
     "FP64", "FP32", "SELF_LOOPS", "TELEPORT", "WORKLIST", "ROUND", "JACOBI",
@@ -124,6 +124,8 @@ def load():
             "dfpr_get_part_times": (st, [vp, vp]),
             "dfpr_server_create": (st, [vp, ctypes.POINTER(Params), i32, ctypes.c_double,
                                         ctypes.POINTER(vp)]),
+            "dfpr_server_create_units": (st, [i32, vp, ctypes.POINTER(Params), i32,
+                                              ctypes.c_double, i32, ctypes.POINTER(vp)]),
             "dfpr_server_submit": (st, [vp, i32, i64, vp, vp, i64, vp, vp, ctypes.POINTER(i64)]),
             "dfpr_server_wait": (st, [vp, i64, ctypes.POINTER(RequestInfo)]),
             "dfpr_server_drain": (st, [vp]),
@@ -146,6 +148,8 @@ def load():
             "dfpr_last_error": (ctypes.c_char_p, []),
             "dfpr_version": (i32, []),
             "dfpr_kernel_launches": (i64, []),
+            "dfpr_residual": (st, [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
             "dfpr_static_pagerank_noalloc": (st, [i32, vp, vp, vp, ctypes.c_double,
                                                   ctypes.c_double, i32, vp,
                                                   ctypes.POINTER(i32), vp]),
@@ -297,6 +301,9 @@ class Graph:
     def set_ranks(self, *a, **k):
         return set_ranks(self, *a, **k)
 
+    def residual(self, *a, **k):
+        return residual(self, *a, **k)
+
     def get_csr(self, *a, **k):
         return get_csr(self, *a, **k)
 
@@ -447,6 +454,14 @@ def get_ranks(g: Graph, out=None):
     return out
 
 
+def residual(g: Graph, alpha: float = 0.85):
+    """dfpr_residual -> (max_v |Eq. 1 (v) - R[v]|, the same relative to R[v]),
+    both computed in FP64 from the stored ranks."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().dfpr_residual(g.handle, float(alpha), ctypes.byref(a), ctypes.byref(b)), "residual")
+    return a.value, b.value
+
+
 def set_ranks(g: Graph, ranks):
     """dfpr_set_ranks from a float64 array (numpy, or torch on the host or the
     graph's device)."""
@@ -491,13 +506,15 @@ def initial_affected(g: Graph, out=None):
 
 
 class Server:
-    """dfpr_server_*: a native server thread serving update requests on a graph
-    (set). submit() queues one graph's batch (host arrays, local ids) and returns
-    a request id; wait() blocks until its cycle is done."""
+    """dfpr_server_*: native worker threads serving update requests on one or
+    more resident units (graphs or sets). submit() queues one graph's batch
+    (host arrays, local ids; parts numbered over the units in order) and
+    returns a request id; wait() blocks until the update that served it is done."""
 
-    def __init__(self, handle: int, graph: Graph):
+    def __init__(self, handle: int, units):
         self._h = handle
-        self.graph = graph
+        self.units = list(units)
+        self.graph = self.units[0]
 
     def submit(self, part, del_src, del_dst, ins_src, ins_dst) -> int:
         """dfpr_server_submit: queues one batch for graph `part` -> request id."""
@@ -511,7 +528,7 @@ class Server:
         return int(rid.value)
 
     def wait(self, request_id: int) -> RequestInfo:
-        """dfpr_server_wait: blocks until the request's cycle finished."""
+        """dfpr_server_wait: blocks until the update that served the request finished."""
         info = RequestInfo()
         _check(load().dfpr_server_wait(self._h, int(request_id), ctypes.byref(info)), "server_wait")
         return info
@@ -521,8 +538,8 @@ class Server:
         _check(load().dfpr_server_drain(self._h), "server_drain")
 
     def destroy(self):
-        """dfpr_server_destroy: drains, stops the thread and frees the server (the
-        graph stays)."""
+        """dfpr_server_destroy: drains, stops the worker threads and frees the
+        server (the units stay)."""
         h, self._h = self._h, None
         if h:
             _check(load().dfpr_server_destroy(h), "server_destroy")
@@ -534,16 +551,23 @@ class Server:
             pass
 
 
-def server_create(g: Graph, params: Params | None = None, max_slots: int = 64,
-                  mem_fraction: float = 0.5) -> Server:
-    """dfpr_server_create: starts a server thread on g; a cycle admits up to
-    max_slots queued requests while their batches fit mem_fraction of the
-    device's free memory, and updates them in one launch."""
+def server_create(g, params: Params | None = None, max_slots: int = 64,
+                  mem_fraction: float = 0.5, grid_share: int = 0) -> Server:
+    """dfpr_server_create_units over g (a Graph, or a list of Graphs each with
+    its own stream): a unit's worker admits its queued requests whenever the
+    unit is idle, at most max_slots in flight over the server and while their
+    batches fit mem_fraction of the device's free memory, and updates them in
+    one launch; units update concurrently. grid_share > 0 caps each launch at
+    that many CTAs so that several units' launches fit on the GPU together."""
+    units = list(g) if isinstance(g, (list, tuple)) else [g]
+    arr = (ctypes.c_void_p * len(units))(*[u.handle for u in units])
     h = ctypes.c_void_p()
-    _check(load().dfpr_server_create(g.handle, ctypes.byref(params) if params is not None else None,
-                                     int(max_slots), float(mem_fraction), ctypes.byref(h)),
+    _check(load().dfpr_server_create_units(len(units), arr,
+                                           ctypes.byref(params) if params is not None else None,
+                                           int(max_slots), float(mem_fraction), int(grid_share),
+                                           ctypes.byref(h)),
            "server_create")
-    return Server(h.value, g)
+    return Server(h.value, units)
 
 
 def set_allocator(alloc=None, free=None, ctx=None):

@@ -578,6 +578,27 @@ dfpr_status dfpr_static_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats
   API_END
 }
 
+dfpr_status dfpr_residual(const dfpr_graph* gc, double alpha, double* linf, double* linf_rel) {
+  if (!gc || !linf) {
+    set_error("dfpr_residual: NULL argument");
+    return DFPR_EINVAL;
+  }
+  if (!(alpha > 0.0 && alpha < 1.0)) {
+    set_error("dfpr_residual: need 0 < alpha < 1");
+    return DFPR_EINVAL;
+  }
+  dfpr_graph* g = const_cast<dfpr_graph*>(gc);
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  double a = 0.0, b = 0.0;
+  residual(g, alpha, &a, &b);
+  *linf = a;
+  if (linf_rel) *linf_rel = b;
+  return DFPR_OK;
+  API_END
+}
+
 dfpr_status dfpr_get_ranks(const dfpr_graph* gc, double* out, int on_device) {
   if (!gc || !out) {
     set_error("dfpr_get_ranks: NULL argument");
@@ -601,9 +622,9 @@ dfpr_status dfpr_get_ranks(const dfpr_graph* gc, double* out, int on_device) {
       dst = tmp.p;
     }
     if (g->cfg.precision == DFPR_FP64)
-      k_ranks_out<double><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(g->R64.p, perm, dst, n);
+      k_ranks_out<double><<<blocks_for(n, kNT, sm_cap(16u)), kNT, 0, s>>>(g->R64.p, perm, dst, n);
     else
-      k_ranks_out<float><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(g->R32.p, perm, dst, n);
+      k_ranks_out<float><<<blocks_for(n, kNT, sm_cap(16u)), kNT, 0, s>>>(g->R32.p, perm, dst, n);
     DFPR_LAUNCHED();
     if (!on_device)
       DFPR_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -632,9 +653,9 @@ dfpr_status dfpr_set_ranks(dfpr_graph* g, const double* ranks, int on_device) {
     DevArray<double> tmp;
     const double* srcp = stage_in(g, tmp, ranks, n, on_device);
     if (g->cfg.precision == DFPR_FP64)
-      k_ranks_in<double><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(srcp, perm, g->R64.p, n);
+      k_ranks_in<double><<<blocks_for(n, kNT, sm_cap(16u)), kNT, 0, s>>>(srcp, perm, g->R64.p, n);
     else
-      k_ranks_in<float><<<blocks_for(n, kNT, 152u * 16u), kNT, 0, s>>>(srcp, perm, g->R32.p, n);
+      k_ranks_in<float><<<blocks_for(n, kNT, sm_cap(16u)), kNT, 0, s>>>(srcp, perm, g->R32.p, n);
     DFPR_LAUNCHED();
   }
   refresh_contributions(g);

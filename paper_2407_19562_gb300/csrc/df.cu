@@ -1726,7 +1726,49 @@ __global__ void k_seed_round(int32_t n, long long stride, int32_t* alist, DfCtl*
   }
 }
 
-unsigned grid_small(long long n) { return blocks_for(n, kNT, 152u * 16u); }
+// Residual of Eq. 1 at every vertex, in FP64 from the stored ranks (not the
+// stored contributions): r'(v) = (1 - alpha) / n_v + alpha * (sum over in-edges
+// (u, v) of R[u] / |out(u)| + dead / n), with n_v the vertex count of v's graph
+// and dead the dead-end mass (0 with self-loops). A warp per vertex; the
+// largest |r'(v) - R[v]| and |r'(v) - R[v]| / R[v] go to out[0] and out[1] as
+// bit patterns (non-negative doubles order like their bits).
+template <class T>
+__global__ void k_residual(int32_t n, const RowDesc* __restrict__ in_rows,
+                           const int32_t* __restrict__ in_edges,
+                           const RowDesc* __restrict__ out_rows, const T* __restrict__ R,
+                           const int32_t* __restrict__ part_off, int nparts, double alpha,
+                           const double* dead, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const double tele = dead ? *dead / (double)n : 0.0;
+  double worst = 0.0, worst_rel = 0.0;
+  for (long long v = warp; v < n; v += nw) {
+    const RowDesc row = load_row(in_rows + v);
+    double s = 0.0;
+    for (long long e = lane; e < row.deg; e += 32) {
+      const int u = __ldg(in_edges + row.off + e);
+      s += (double)R[u] / (double)out_rows[u].deg;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
+    double nv = (double)n;
+    if (nparts > 1) {
+      const int p = part_of(part_off, nparts, (int)v);
+      nv = (double)(__ldg(part_off + p + 1) - __ldg(part_off + p));
+    }
+    const double r = (1.0 - alpha) / nv + alpha * (s + tele);
+    const double res = fabs(r - (double)R[v]);
+    worst = fmax(worst, res);
+    worst_rel = fmax(worst_rel, res / fabs((double)R[v]));
+  }
+  if (lane == 0) {
+    if (worst > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(worst));
+    if (worst_rel > 0.0) atomicMax(out + 1, (unsigned long long)__double_as_longlong(worst_rel));
+  }
+}
+
+unsigned grid_small(long long n) { return blocks_for(n, kNT, sm_cap(16u)); }
 
 // ---------------------------------------------------------------------------
 // Host drivers
@@ -2293,6 +2335,36 @@ double dangling_mass(dfpr_graph* g) {
   double d;
   memcpy(&d, &bits, sizeof d);
   return d;
+}
+
+void residual(dfpr_graph* g, double alpha, double* linf, double* linf_rel) {
+  cudaStream_t s = g->stream;
+  unsigned long long* out = g->host_sync.p + 12;  // two words, cleared here
+  double* dead = nullptr;
+  if (g->cfg.dead_end == DFPR_TELEPORT) {
+    dead = (double*)(g->host_sync.p + 14);
+    DFPR_CUDA(cudaMemsetAsync(dead, 0, sizeof(double), s));
+    if (g->cfg.precision == DFPR_FP64)
+      k_dangling<double><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R64.p, dead);
+    else
+      k_dangling<float><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, g->R32.p, dead);
+    DFPR_LAUNCHED();
+  }
+  DFPR_CUDA(cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s));
+  const unsigned grid = blocks_for(32ll * g->n, kNT, sm_cap(16u));
+  const int32_t* poff = g->nparts > 1 ? g->part_off.p : nullptr;
+  if (g->cfg.precision == DFPR_FP64)
+    k_residual<double><<<grid, kNT, 0, s>>>(g->n, g->in.rows.p, g->in.edges.p, g->out.rows.p,
+                                            g->R64.p, poff, g->nparts, alpha, dead, out);
+  else
+    k_residual<float><<<grid, kNT, 0, s>>>(g->n, g->in.rows.p, g->in.edges.p, g->out.rows.p,
+                                           g->R32.p, poff, g->nparts, alpha, dead, out);
+  DFPR_LAUNCHED();
+  unsigned long long b[2];
+  DFPR_CUDA(cudaMemcpyAsync(b, out, sizeof b, cudaMemcpyDeviceToHost, s));
+  DFPR_CUDA(cudaStreamSynchronize(s));
+  memcpy(linf, &b[0], sizeof(double));
+  memcpy(linf_rel, &b[1], sizeof(double));
 }
 
 dfpr_status run_iteration(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st) {

@@ -30,4 +30,8 @@ double rank_sum(dfpr_graph* g);
 // FP64 sum of the ranks of dead ends (vertices without out-edges).
 double dangling_mass(dfpr_graph* g);
 
+// Largest residual of Eq. 1 over all vertices, absolute and relative to the
+// vertex's rank, computed in FP64 from the stored ranks.
+void residual(dfpr_graph* g, double alpha, double* linf, double* linf_rel);
+
 }  // namespace dfpr

@@ -497,7 +497,7 @@ __global__ void k_max_degree(const RowDesc* __restrict__ rows, int32_t n, unsign
   if ((threadIdx.x & 31) == 0 && d > 0) atomicMax(out, d);
 }
 
-unsigned grid_for(long long n) { return blocks_for(n, NT, 152u * 32u); }
+unsigned grid_for(long long n) { return blocks_for(n, NT, sm_cap(32u)); }
 
 }  // namespace
 

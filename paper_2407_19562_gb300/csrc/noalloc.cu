@@ -6,18 +6,28 @@
 //
 // The entry point is a variant of the library's Jacobi iteration: instead of
 // vectors it allocates per graph, it keeps its scratch (the second rank
-// vector, both contribution vectors and a reduction word) in one file-scope
-// __device__ array of fixed size. That array exists on every GPU that loads
-// this library and stays allocated until the process exits, which is why its
-// size is capped at kNoAllocMaxVertices vertices (3 * 8 MiB + 256 bytes).
+// vector, both contribution vectors and three control words) in one
+// file-scope __device__ array of fixed size. That array exists on every GPU
+// that loads this library and stays allocated until the process exits, which
+// is why its size is capped at kNoAllocMaxVertices vertices
+// (3 * 8 MiB + 256 bytes).
+//
+// Vertices without out-edges (dead ends) spread their rank uniformly, as the
+// library does for graphs loaded with DFPR_TELEPORT: every iteration adds
+// alpha * D / n to each rank, D being the rank held by dead ends in the
+// previous iterate, summed in FP64. A graph with a self-loop on every vertex
+// has no dead ends, so the term is zero there.
 //
 // Host code cannot use the array's symbol as a device address: on the host it
 // names a host-side stand-in. The device address is fetched once per device
 // with cudaGetSymbolAddress (with that device current) on the first call made
 // on that device, so that first call should happen before any stream capture.
-// Every call shares the array and its previous contents: the reduction word is
-// cleared before each iteration, and calls that overlap on the GPU (two
-// streams, two threads) race on the array and must not be issued.
+// The cached address belongs to the device's current context: a
+// cudaDeviceReset between calls (which also frees every other device
+// allocation of the process) invalidates it. Every call shares the array and
+// its previous contents: the control words are cleared before they are used,
+// and calls that overlap on the GPU (two streams, two threads) race on the
+// array and must not be issued.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,6 +36,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "primitives.cuh"
 
 namespace dfpr {
 namespace {
@@ -59,45 +70,57 @@ unsigned char* scratch_address(int dev) {
 constexpr int kNT = 256;
 
 __global__ void k_na_init(int32_t n, const int32_t* __restrict__ outdeg, double* __restrict__ R,
-                          double* __restrict__ C) {
+                          double* __restrict__ C, double* __restrict__ dsum) {
   const double r0 = 1.0 / (double)n;
+  double dead = 0.0;
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (long long)gridDim.x * blockDim.x) {
     R[u] = r0;
     const int d = outdeg[u];
     C[u] = d > 0 ? r0 / (double)d : 0.0;
+    if (d == 0) dead += r0;
   }
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) dead += __shfl_down_sync(0xffffffffu, dead, k);
+  if ((threadIdx.x & 31) == 0 && dead > 0.0) atomicAdd(dsum, dead);
 }
 
-// One Jacobi iteration of Eq. 1, a warp per vertex: Rn[v] and Cn[v] from C;
-// the largest |Rn[v] - R[v]| goes to *max_bits (non-negative doubles order
-// like their bit patterns).
+// One Jacobi iteration of Eq. 1, a warp per vertex: Rn[v] and Cn[v] from C,
+// with the dead-end term alpha * D / n (D = *dsum, the previous iterate's
+// dead-end mass); the rank of every dead end of the new iterate is added to
+// *dsum_next, and the largest |Rn[v] - R[v]| goes to *max_bits (non-negative
+// doubles order like their bit patterns).
 __global__ void __launch_bounds__(kNT) k_na_iter(int32_t n, const long long* __restrict__ off,
                                                  const int32_t* __restrict__ idx,
                                                  const int32_t* __restrict__ outdeg, double alpha,
                                                  double base, const double* __restrict__ R,
                                                  const double* __restrict__ C,
                                                  double* __restrict__ Rn, double* __restrict__ Cn,
+                                                 const double* __restrict__ dsum,
+                                                 double* __restrict__ dsum_next,
                                                  unsigned long long* max_bits) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  double local_max = 0.0;
+  const double teleport = *dsum / (double)n;
+  double local_max = 0.0, dead = 0.0;
   for (long long v = warp; v < n; v += nw) {
     double s = 0.0;
     for (long long e = off[v] + lane; e < off[v + 1]; e += 32) s += C[idx[e]];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
     if (lane == 0) {
-      const double r = base + alpha * s;
+      const double r = base + alpha * (s + teleport);
       Rn[v] = r;
       const int od = outdeg[v];
       Cn[v] = od > 0 ? r / (double)od : 0.0;
+      if (od == 0) dead += r;
       local_max = fmax(local_max, fabs(r - R[v]));
     }
   }
   if (lane == 0 && local_max > 0.0)
     atomicMax(max_bits, (unsigned long long)__double_as_longlong(local_max));
+  if (lane == 0 && dead > 0.0) atomicAdd(dsum_next, dead);
 }
 
 }  // namespace
@@ -131,23 +154,28 @@ extern "C" dfpr_status dfpr_static_pagerank_noalloc(int32_t n, const int64_t* in
     DFPR_REQUIRE(dev >= 0 && dev < kMaxDevices, DFPR_EINVAL, "device id out of range");
     unsigned char* base_ptr = scratch_address(dev);
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    // control words: [0] the largest change, [1] and [2] the dead-end masses
+    // of the current and the next iterate (they swap every iteration)
     unsigned long long* max_bits = (unsigned long long*)base_ptr;
+    double* dsum = (double*)(base_ptr + 8);
+    double* dsum_next = (double*)(base_ptr + 16);
     double* C = (double*)(base_ptr + kCtlBytes);
     double* Cn = C + kNoAllocMaxVertices;
     double* Rn = Cn + kNoAllocMaxVertices;
     double* Rcur = ranks;  // the caller's buffer holds one of the two rank vectors
     double* Rnext = Rn;
-    const unsigned grid = (unsigned)std::min<long long>((n + kNT / 32 - 1) / (kNT / 32), 152ll * 64);
-    k_na_init<<<std::min<unsigned>((n + kNT - 1) / kNT, 152u * 16u), kNT, 0, s>>>(n, out_degree,
-                                                                               Rcur, C);
+    const unsigned grid = (unsigned)std::min<long long>((n + kNT / 32 - 1) / (kNT / 32), sm_cap(64u));
+    DFPR_CUDA(cudaMemsetAsync(dsum, 0, sizeof(double), s));
+    k_na_init<<<blocks_for(n, kNT, sm_cap(16u)), kNT, 0, s>>>(n, out_degree, Rcur, C, dsum);
     DFPR_LAUNCHED();
     const double base = (1.0 - alpha) / (double)n;
     int it = 0;
     bool converged = false;
     for (; it < max_iter;) {
       DFPR_CUDA(cudaMemsetAsync(max_bits, 0, sizeof(unsigned long long), s));
+      DFPR_CUDA(cudaMemsetAsync(dsum_next, 0, sizeof(double), s));
       k_na_iter<<<grid, kNT, 0, s>>>(n, (const long long*)in_offsets, in_idx, out_degree, alpha,
-                                    base, Rcur, C, Rnext, Cn, max_bits);
+                                    base, Rcur, C, Rnext, Cn, dsum, dsum_next, max_bits);
       DFPR_LAUNCHED();
       unsigned long long bits = 0;  // pageable host word: no pinned allocation
       DFPR_CUDA(cudaMemcpyAsync(&bits, max_bits, sizeof bits, cudaMemcpyDeviceToHost, s));
@@ -156,6 +184,7 @@ extern "C" dfpr_status dfpr_static_pagerank_noalloc(int32_t n, const int64_t* in
       memcpy(&delta, &bits, sizeof delta);
       std::swap(Rcur, Rnext);
       std::swap(C, Cn);
+      std::swap(dsum, dsum_next);
       ++it;
       if (delta <= tol) {
         converged = true;

@@ -27,4 +27,11 @@ inline unsigned blocks_for(long long n, int per_block, unsigned cap = 1u << 30) 
   return (unsigned)(b > cap ? cap : b);
 }
 
+// Multiprocessors of the current device (queried once per device and cached;
+// 1 when the query fails, so that a grid cap never becomes 0).
+int device_sms();
+
+// Grid-stride cap of `per_sm` CTAs on every multiprocessor of the current device.
+inline unsigned sm_cap(unsigned per_sm) { return (unsigned)device_sms() * per_sm; }
+
 }  // namespace dfpr

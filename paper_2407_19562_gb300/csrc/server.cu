@@ -1,8 +1,17 @@
-// Serving runtime: a thread that keeps a graph (set) resident and serves
-// update requests in cycles; each cycle applies every admitted request's batch
-// and updates all affected graphs with one persistent launch (see dfpr.h).
+// Serving runtime with continuous batching. A server owns one or more
+// resident units (a graph, or a set of graphs from dfpr_graph_load_parts),
+// each with its own stream and one worker thread. A unit's worker admits the
+// unit's queued requests whenever the unit is idle and the server has free
+// slots and memory, applies them, and runs one update over the unit (one
+// persistent launch for every admitted request of that unit). Units update
+// independently, so a request for an idle unit is admitted at once even while
+// other units' updates are on the GPU, and their launches overlap on the
+// device. A unit never changes while its own update reads it (read-only
+// snapshot, Sec. 3.4): requests that arrive for a busy unit join its next
+// update.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -26,7 +35,8 @@ using Clock = std::chrono::steady_clock;
 
 struct Request {
   int64_t id = 0;
-  int32_t part = 0;
+  int32_t unit = 0;  // the unit that holds the graph
+  int32_t part = 0;  // the graph's index within its unit
   std::vector<int32_t> ds, dd, is, id_;
   double submit_ms = 0, admit_ms = 0, done_ms = 0;
   int64_t cycle = -1;
@@ -36,30 +46,39 @@ struct Request {
   int64_t edges() const { return (int64_t)ds.size() + (int64_t)is.size(); }
 };
 
-// Device bytes a cycle needs per batch edge: batch keys and their sort buffer,
-// flags and positions, real-change lists in both orders, row-merge plans.
+// Device bytes an update needs per batch edge: batch keys and their sort
+// buffer, flags and positions, real-change lists in both orders, row-merge plans.
 constexpr double kBytesPerBatchEdge = 160.0;
+
+struct Unit {
+  dfpr_graph* g = nullptr;
+  std::deque<std::shared_ptr<Request>> queue;
+  bool running = false;
+  std::thread th;
+  DevArray<int32_t> dev_batch;  // the update's batch arrays on the device
+  std::vector<int32_t> host_batch;
+};
 
 }  // namespace
 }  // namespace dfpr
 
 struct dfpr_server {
-  dfpr_graph* g = nullptr;
+  std::vector<std::unique_ptr<dfpr::Unit>> units;
+  std::vector<int32_t> part_unit, part_local;  // global part -> (unit, part within it)
   dfpr_params p;
   int32_t max_slots = 64;
   double mem_fraction = 0.5;
+  int grid_share = 0;  // CTAs per launch when units update concurrently (0: full grid)
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<std::shared_ptr<dfpr::Request>> queue;
   std::unordered_map<int64_t, std::shared_ptr<dfpr::Request>> requests;
   int64_t next_id = 1;
   int64_t cycles = 0;
-  bool in_cycle = false;
+  int32_t in_flight = 0;    // admitted requests not yet done
+  int32_t queued = 0;       // requests waiting in unit queues
+  double reserved = 0.0;    // batch bytes of admitted requests
   bool stop = false;
-  std::thread th;
-  dfpr::DevArray<int32_t> dev_batch;  // the cycle's batch arrays on the device
-  std::vector<int32_t> host_batch;
 
   double now_ms() const {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -69,18 +88,18 @@ struct dfpr_server {
 namespace dfpr {
 namespace {
 
-// Applies one layer of requests (at most one per graph) as one batch.
-void apply_layer(dfpr_server* s, const std::vector<std::shared_ptr<Request>>& layer) {
-  dfpr_graph* g = s->g;
+// Applies one layer of requests (at most one per graph of the unit) as one batch.
+void apply_layer(Unit* u, const std::vector<std::shared_ptr<Request>>& layer) {
+  dfpr_graph* g = u->g;
   int64_t nd = 0, ni = 0;
   for (auto& r : layer) {
     nd += (int64_t)r->ds.size();
     ni += (int64_t)r->is.size();
   }
   if (nd + ni == 0) return;
-  // host staging: del_src | del_dst | ins_src | ins_dst in global ids
-  s->host_batch.resize((size_t)(2 * (nd + ni)));
-  int32_t* ds = s->host_batch.data();
+  // host staging: del_src | del_dst | ins_src | ins_dst in the unit's global ids
+  u->host_batch.resize((size_t)(2 * (nd + ni)));
+  int32_t* ds = u->host_batch.data();
   int32_t* dd = ds + nd;
   int32_t* is = dd + nd;
   int32_t* id = is + ni;
@@ -98,38 +117,51 @@ void apply_layer(dfpr_server* s, const std::vector<std::shared_ptr<Request>>& la
     od += (int64_t)r->ds.size();
     oi += (int64_t)r->is.size();
   }
-  s->dev_batch.ensure((size_t)(2 * (nd + ni)), g->stream);
-  DFPR_CUDA(cudaMemcpyAsync(s->dev_batch.p, ds, sizeof(int32_t) * 2 * (nd + ni),
+  u->dev_batch.ensure((size_t)(2 * (nd + ni)), g->stream);
+  DFPR_CUDA(cudaMemcpyAsync(u->dev_batch.p, ds, sizeof(int32_t) * 2 * (nd + ni),
                             cudaMemcpyHostToDevice, g->stream));
-  const int32_t* d = s->dev_batch.p;
+  const int32_t* d = u->dev_batch.p;
   long long applied[2] = {0, 0};
   graph_apply(g, d, d + nd, nd, d + 2 * nd, d + 2 * nd + ni, ni, applied);
 }
 
-void serve(dfpr_server* s) {
-  cudaSetDevice(s->g->device);
+// Worker of one unit: admission, update, completion, until the server stops
+// and the unit's queue is empty.
+void serve_unit(dfpr_server* s, Unit* u) {
+  cudaSetDevice(u->g->device);
   while (true) {
     std::vector<std::shared_ptr<Request>> admitted;
+    double need = 0;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
-      if (s->queue.empty()) break;  // stop requested and nothing left
+      s->cv_work.wait(lk, [&] {
+        return (s->stop && u->queue.empty()) ||
+               (!u->queue.empty() && s->in_flight < s->max_slots);
+      });
+      if (u->queue.empty()) break;  // stop requested and nothing left
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         cudaGetLastError();
         free_b = 0;
       }
-      const double budget = s->mem_fraction * (double)free_b;
-      double need = 0;
-      while (!s->queue.empty() && (int32_t)admitted.size() < s->max_slots) {
-        auto& r = s->queue.front();
+      const double budget = s->mem_fraction * (double)free_b - s->reserved;
+      while (!u->queue.empty() && s->in_flight + (int32_t)admitted.size() < s->max_slots) {
+        auto& r = u->queue.front();
         const double b = kBytesPerBatchEdge * (double)r->edges();
-        if (!admitted.empty() && need + b > budget) break;  // memory admission
+        // memory admission; with nothing else in flight one request always goes
+        if ((!admitted.empty() || s->in_flight > 0) && need + b > budget) break;
         need += b;
         admitted.push_back(r);
-        s->queue.pop_front();
+        u->queue.pop_front();
       }
-      s->in_cycle = true;
+      if (admitted.empty()) {  // no memory now (so another update is in flight): wait for it
+        s->cv_work.wait(lk);
+        continue;
+      }
+      s->in_flight += (int32_t)admitted.size();
+      s->queued -= (int32_t)admitted.size();
+      s->reserved += need;
+      u->running = true;
     }
     const double t_admit = s->now_ms();
     dfpr_status st = DFPR_OK;
@@ -143,9 +175,11 @@ void serve(dfpr_server* s) {
         if ((int)layers.size() <= k) layers.resize(k + 1);
         layers[k].push_back(r);
       }
-      for (auto& layer : layers) apply_layer(s, layer);
+      for (auto& layer : layers) apply_layer(u, layer);
+      dfpr_params p = s->p;
+      if (p.grid_ctas == 0 && s->grid_share > 0) p.grid_ctas = s->grid_share;
       dfpr_stats stats;
-      st = run_update(s->g, &s->p, &stats, kRunDF);
+      st = run_update(u->g, &p, &stats, kRunDF);
     } catch (const Fail& f) {
       st = f.st;
     } catch (...) {
@@ -163,9 +197,13 @@ void serve(dfpr_server* s) {
         r->done = true;
       }
       ++s->cycles;
-      s->in_cycle = false;
+      s->in_flight -= (int32_t)admitted.size();
+      s->reserved -= need;
+      if (s->in_flight == 0) s->reserved = 0.0;  // no drift from rounding
+      u->running = false;
     }
     s->cv_done.notify_all();
+    s->cv_work.notify_all();  // slots and memory are free again
   }
 }
 
@@ -175,6 +213,18 @@ bool ids_ok(const int32_t* a, int64_t n, int32_t lim) {
   return true;
 }
 
+void release_units(dfpr_server* s) {
+  for (auto& u : s->units) {
+    if (!u->g) continue;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(u->g->device);
+    u->dev_batch.release();
+    if (prev >= 0) cudaSetDevice(prev);
+    u->g->busy.store(0);
+  }
+}
+
 }  // namespace
 }  // namespace dfpr
 
@@ -182,56 +232,105 @@ using namespace dfpr;
 
 extern "C" {
 
-dfpr_status dfpr_server_create(dfpr_graph* g, const dfpr_params* p, int32_t max_slots,
-                               double mem_fraction, dfpr_server** out) {
+dfpr_status dfpr_server_create_units(int32_t k, dfpr_graph* const* units, const dfpr_params* p,
+                                     int32_t max_slots, double mem_fraction, int32_t grid_share,
+                                     dfpr_server** out) {
   if (out) *out = nullptr;
-  if (!g || !out || max_slots < 1 || !(mem_fraction > 0.0 && mem_fraction <= 1.0)) {
-    set_error("dfpr_server_create: need a graph, max_slots >= 1 and 0 < mem_fraction <= 1");
+  if (k < 1 || !units || !out || max_slots < 1 || !(mem_fraction > 0.0 && mem_fraction <= 1.0) ||
+      grid_share < 0) {
+    set_error("dfpr_server_create: need k >= 1 units, max_slots >= 1, 0 < mem_fraction <= 1 "
+              "and grid_share >= 0");
     return DFPR_EINVAL;
   }
-  int z = 0;
-  if (!g->busy.compare_exchange_strong(z, 1)) {
-    set_error("dfpr_server_create: another call on this graph is in progress");
+  for (int32_t i = 0; i < k; ++i) {
+    if (!units[i]) {
+      set_error("dfpr_server_create: a unit is NULL");
+      return DFPR_EINVAL;
+    }
+    for (int32_t j = 0; j < i; ++j)
+      if (units[j] == units[i]) {
+        set_error("dfpr_server_create: a unit is given twice");
+        return DFPR_EINVAL;
+      }
+  }
+  // take every unit, or none
+  int32_t taken = 0;
+  for (; taken < k; ++taken) {
+    int z = 0;
+    if (!units[taken]->busy.compare_exchange_strong(z, 1)) break;
+  }
+  if (taken < k) {
+    for (int32_t j = 0; j < taken; ++j) units[j]->busy.store(0);
+    set_error("dfpr_server_create: another call on a unit is in progress");
     return DFPR_EBUSY;
   }
   dfpr_server* s = nullptr;
   try {
     s = new dfpr_server();
+    for (int32_t i = 0; i < k; ++i) {
+      s->units.emplace_back(new Unit());
+      s->units.back()->g = units[i];
+      for (int32_t j = 0; j < units[i]->nparts; ++j) {
+        s->part_unit.push_back(i);
+        s->part_local.push_back(j);
+      }
+    }
   } catch (...) {
-    g->busy.store(0);
+    for (int32_t j = 0; j < k; ++j) units[j]->busy.store(0);
+    delete s;
     set_error("host allocation failed");
     return DFPR_ENOMEM;
   }
-  s->g = g;
   if (p) s->p = *p;
   else dfpr_default_params(&s->p);
   s->max_slots = max_slots;
   s->mem_fraction = mem_fraction;
+  s->grid_share = grid_share;
   s->t0 = Clock::now();
+  size_t started = 0;
   try {
-    s->th = std::thread(serve, s);
+    for (; started < s->units.size(); ++started) {
+      Unit* u = s->units[started].get();
+      u->th = std::thread(serve_unit, s, u);
+    }
   } catch (...) {
-    g->busy.store(0);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (size_t i = 0; i < started; ++i) s->units[i]->th.join();
+    release_units(s);
     delete s;
-    set_error("dfpr_server_create: could not start the server thread");
+    set_error("dfpr_server_create: could not start the worker threads");
     return DFPR_ENOMEM;
   }
   *out = s;
   return DFPR_OK;
 }
 
+dfpr_status dfpr_server_create(dfpr_graph* g, const dfpr_params* p, int32_t max_slots,
+                               double mem_fraction, dfpr_server** out) {
+  if (out) *out = nullptr;
+  if (!g) {
+    set_error("dfpr_server_create: need a graph");
+    return DFPR_EINVAL;
+  }
+  return dfpr_server_create_units(1, &g, p, max_slots, mem_fraction, 0, out);
+}
+
 dfpr_status dfpr_server_submit(dfpr_server* s, int32_t part, int64_t n_del, const int32_t* del_src,
                                const int32_t* del_dst, int64_t n_ins, const int32_t* ins_src,
                                const int32_t* ins_dst, int64_t* request_id) {
   if (request_id) *request_id = 0;
-  if (!s || part < 0 || part >= s->g->nparts || n_del < 0 || n_ins < 0 ||
+  if (!s || part < 0 || part >= (int32_t)s->part_unit.size() || n_del < 0 || n_ins < 0 ||
       (n_del > 0 && (!del_src || !del_dst)) || (n_ins > 0 && (!ins_src || !ins_dst))) {
     set_error("dfpr_server_submit: invalid arguments");
     return DFPR_EINVAL;
   }
-  const int32_t lim = s->g->nparts > 1
-                          ? s->g->part_off_host[part + 1] - s->g->part_off_host[part]
-                          : s->g->n;
+  const int32_t ui = s->part_unit[part], lp = s->part_local[part];
+  const dfpr_graph* g = s->units[ui]->g;
+  const int32_t lim = g->nparts > 1 ? g->part_off_host[lp + 1] - g->part_off_host[lp] : g->n;
   if (!ids_ok(del_src, n_del, lim) || !ids_ok(del_dst, n_del, lim) || !ids_ok(ins_src, n_ins, lim) ||
       !ids_ok(ins_dst, n_ins, lim)) {
     set_error("dfpr_server_submit: a vertex id is outside its graph");
@@ -240,7 +339,8 @@ dfpr_status dfpr_server_submit(dfpr_server* s, int32_t part, int64_t n_del, cons
   std::shared_ptr<Request> r;
   try {
     r = std::make_shared<Request>();
-    r->part = part;
+    r->unit = ui;
+    r->part = lp;
     r->ds.assign(del_src, del_src + n_del);
     r->dd.assign(del_dst, del_dst + n_del);
     r->is.assign(ins_src, ins_src + n_ins);
@@ -258,9 +358,10 @@ dfpr_status dfpr_server_submit(dfpr_server* s, int32_t part, int64_t n_del, cons
     r->id = s->next_id++;
     r->submit_ms = s->now_ms();
     s->requests[r->id] = r;
-    s->queue.push_back(r);
+    s->units[ui]->queue.push_back(r);
+    ++s->queued;
   }
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();
   if (request_id) *request_id = r->id;
   return DFPR_OK;
 }
@@ -296,7 +397,7 @@ dfpr_status dfpr_server_drain(dfpr_server* s) {
     return DFPR_EINVAL;
   }
   std::unique_lock<std::mutex> lk(s->mu);
-  s->cv_done.wait(lk, [&] { return s->queue.empty() && !s->in_cycle; });
+  s->cv_done.wait(lk, [&] { return s->queued == 0 && s->in_flight == 0; });
   return DFPR_OK;
 }
 
@@ -307,17 +408,10 @@ dfpr_status dfpr_server_destroy(dfpr_server* s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->th.joinable()) s->th.join();
-  dfpr_graph* g = s->g;
-  {
-    int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(g->device);
-    s->dev_batch.release();
-    if (prev >= 0) cudaSetDevice(prev);
-  }
+  for (auto& u : s->units)
+    if (u->th.joinable()) u->th.join();
+  release_units(s);
   delete s;
-  g->busy.store(0);
   return DFPR_OK;
 }
 

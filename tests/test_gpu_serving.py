@@ -85,3 +85,65 @@ def test_server_rejects_bad_requests(gpu_lib, served):
     srv.drain()
     srv.destroy()
     s.get_ranks()  # usable again once the server is gone
+
+
+def test_units_update_continuously_and_match_oracle(gpu_lib, served):
+    # every graph its own unit (own stream, own worker): requests are admitted
+    # whenever their graph is idle, not at cycle boundaries, and the results
+    # are those of the set served in cycles and of the oracle
+    graphs, off, _, _, reqs = served
+    units = []
+    for g in graphs:
+        h = gpu_lib.graph_load(g["n"], g["src"], g["dst"], stream=None)
+        h.set_ranks(g["ref0"])
+        units.append(h)
+    sms = __import__("torch").cuda.get_device_properties(0).multi_processor_count
+    srv = gpu_lib.server_create(units, max_slots=64, grid_share=2 * sms)
+    ids = [srv.submit(i, *batch) for i, batch in reqs]
+    infos = [srv.wait(r) for r in ids]
+    srv.destroy()
+    assert all(i.status == gpu_lib.OK for i in infos)
+    for i in infos:
+        assert i.submit_ms <= i.admit_ms <= i.done_ms
+    # updates of different units overlapped in time
+    spans = sorted({(i.cycle, i.admit_ms, i.done_ms) for i in infos}, key=lambda t: t[1])
+    assert any(b[1] < a[2] for a, b in zip(spans, spans[1:]))
+    R_mix, _ = serve_all(gpu_lib, served, max_slots=64)
+    for k, g in enumerate(graphs):
+        R = units[k].get_ranks()
+        assert np.max(np.abs(R - g["ref1"])) <= LINF64, k
+        assert np.max(np.abs(R - R_mix[off[k]:off[k + 1]])) <= LINF64, k
+
+
+def test_request_for_an_idle_unit_is_admitted_during_another_update(gpu_lib):
+    import time
+    big_n, big_s, big_d = workloads.rmat_graph(17, 16, 41)
+    small_n, small_s, small_d = workloads.rmat_graph_n(3000, 8.0, 42)
+    o_big = oracle.Graph.build(big_n, big_s, big_d)
+    o_small = oracle.Graph.build(small_n, small_s, small_d)
+    R_big, _ = o_big.reference()
+    R_small, _ = o_small.reference()
+    big_batch = workloads.uniform_batch(big_n, 60000, 43, big_s, big_d)
+    small_batch = workloads.uniform_batch(small_n, 50, 44, small_s, small_d)
+    ref_big, _ = o_big.apply(*big_batch)[0].reference()
+    ref_small, _ = o_small.apply(*small_batch)[0].reference()
+    a = gpu_lib.graph_load(big_n, big_s, big_d, stream=None)
+    b = gpu_lib.graph_load(small_n, small_s, small_d, stream=None)
+    a.set_ranks(R_big)
+    b.set_ranks(R_small)
+    sms = __import__("torch").cuda.get_device_properties(0).multi_processor_count
+    srv = gpu_lib.server_create([a, b], max_slots=8, grid_share=2 * sms)
+    ra = srv.submit(0, *big_batch)
+    # wait until the big update is running, then submit for the idle unit
+    t0 = time.perf_counter()
+    time.sleep(0.002)
+    rb = srv.submit(1, *small_batch)
+    ib, ia = srv.wait(rb), srv.wait(ra)
+    srv.destroy()
+    assert ia.status == gpu_lib.OK and ib.status == gpu_lib.OK
+    assert ib.submit_ms < ia.done_ms, "the small request arrived after the big update ended"
+    assert ib.admit_ms < ia.done_ms          # admitted while the other update ran
+    assert ib.cycle != ia.cycle
+    assert np.max(np.abs(a.get_ranks() - ref_big)) <= LINF64
+    assert np.max(np.abs(b.get_ranks() - ref_small)) <= LINF64
+    assert time.perf_counter() - t0 < 60
