@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--mode", choices=["worklist", "round", "jacobi"], default="worklist")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="rmat24: skip the FP32, grid, many-graph and serving keys of the line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-scale", type=int, default=18)
     ap.add_argument("--timeout-ms", type=float, default=60000.0)
@@ -174,6 +176,31 @@ def phase_share(stats):
     return {k: round(v / all_, 4) for k, v in tot.items()}
 
 
+def host_residual(R, in_off, in_idx, part_off=None, alpha=0.85, sample=200_000, seed=0):
+    """Largest |Eq. 1 (v) - R[v]| and |Eq. 1 (v) - R[v]| / R[v] over sampled
+    vertices, evaluated with numpy in FP64 from exported in-rows (caller ids)
+    and ranks; out-degrees are counted from the in-rows. part_off: vertex
+    offsets of the graphs of a set (each graph its own n in the teleport term)."""
+    n = len(R)
+    outdeg = np.bincount(in_idx, minlength=n).astype(np.float64)
+    contrib = np.where(outdeg > 0, R / np.maximum(outdeg, 1.0), 0.0)
+    rng = np.random.default_rng(seed)
+    v = np.unique(rng.integers(0, n, size=min(sample, n)))
+    lo, hi = in_off[v], in_off[v + 1]
+    lens = (hi - lo).astype(np.int64)
+    idx = np.repeat(lo - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens) + np.arange(lens.sum())
+    sums = np.zeros(len(v))
+    np.add.at(sums, np.repeat(np.arange(len(v)), lens), contrib[in_idx[idx]])
+    if part_off is None:
+        nv = np.full(len(v), float(n))
+    else:
+        po = np.asarray(part_off, np.int64)
+        k = np.searchsorted(po, v, side="right") - 1
+        nv = (po[k + 1] - po[k]).astype(np.float64)
+    res = np.abs((1.0 - alpha) / nv + alpha * sums - R[v])
+    return float(res.max()), float((res / R[v]).max()), int(len(v))
+
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_worklist
 # launch from an ncu capture of the same workload, kept with a hash of the
 # kernel's sources: a figure is reported only while the sources are unchanged.
@@ -260,14 +287,33 @@ def oracle_sample(spec, cpu_scale: int, batch_frac: float, steps: int, seed0: in
     return times, factor, desc
 
 
-def cpu_baseline_entry(times, factor, desc, cores=1):
+def cpu_baseline_entry(times, factor, desc, cores=1, growth=None):
+    """The oracle's time per batch at the workload's size, from a bounded sample:
+    scaled by the measured growth curve when one is given (growth =
+    (value, growth per scale, smaller sample's ms)), else by the ratio of edge
+    draws (a lower bound)."""
     sample_ms = statistics.mean(times)
-    return {"value": sample_ms * factor, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": desc, "sample_ms_per_batch": sample_ms, "scale_factor": factor,
-            "cpu": cpu_model()}
+    e = {"value": sample_ms * factor, "unit": UNIT, "cores": cores, "kind": "oracle",
+         "sample": desc, "sample_ms_per_batch": sample_ms, "scale_factor": factor,
+         "extrapolated": factor != 1.0, "linear_lower_bound": sample_ms * factor,
+         "cpu": cpu_model(), "host_cpus": os.cpu_count()}
+    if growth is not None:
+        e["value"], e["growth_per_scale"], e["smaller_sample_ms_per_batch"] = growth
+        e["scale_factor"] = e["value"] / sample_ms
+        e["extrapolation"] = "measured growth curve: two samples two R-MAT scales apart"
+    return e
 
 
 def cpu_model():
+    """Model name of the host CPU: lscpu's "Model name" (Arm hosts name the core
+    there, e.g. Neoverse-V2), else /proc/cpuinfo's model name or part number."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
@@ -276,6 +322,20 @@ def cpu_model():
     except OSError:
         pass
     return "unknown"
+
+
+def growth_extrapolation(spec, cpu_scale, batch_frac, sample_ms):
+    """Extrapolates the oracle's ms per batch from the sample's scale to the
+    workload's by a measured growth curve: one more sample two R-MAT scales
+    below gives the growth per scale, g = (t(s) / t(s - 2))^(1/2), and the
+    workload's time is t(s) * g^(S - s). Returns (value, g, the smaller
+    sample's ms per batch) or None for non-R-MAT workloads."""
+    if spec["kind"] != "rmat" or cpu_scale - 2 < 10 or spec["scale"] <= cpu_scale:
+        return None
+    small, _, _ = oracle_sample(spec, cpu_scale - 2, batch_frac, 2, seed0=140)
+    t_small = statistics.mean(small)
+    g = (sample_ms / t_small) ** 0.5 if t_small > 0 else 2.0
+    return sample_ms * g ** (spec["scale"] - cpu_scale), g, t_small
 
 
 # --------------------------------------------------------------------------
@@ -319,7 +379,9 @@ def run_reference(args):
     spec = WORKLOADS[args.workload]
     times, factor, desc = oracle_sample(spec, args.cpu_scale, args.batch_frac,
                                         args.warmup + args.steps)
-    cpu = cpu_baseline_entry(times[args.warmup:], factor, desc)
+    growth = growth_extrapolation(spec, args.cpu_scale, args.batch_frac,
+                                  statistics.mean(times[args.warmup:]))
+    cpu = cpu_baseline_entry(times[args.warmup:], factor, desc, growth=growth)
     v = cpu["value"]
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -433,7 +495,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         times, factor, desc = oracle_sample(spec, args.cpu_scale, args.batch_frac, 2)
-        cpu = cpu_baseline_entry(times, factor, desc)
+        growth = growth_extrapolation(spec, args.cpu_scale, args.batch_frac, statistics.mean(times))
+        cpu = cpu_baseline_entry(times, factor, desc, growth=growth)
 
     if rank != 0:
         if ws > 1:
@@ -450,6 +513,10 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}-batch{args.batch_frac:g}", "n": n, "m": m0,
                    "batch_edges": b, "insert_frac": 0.8, "precision": args.precision,
                    "mode": args.mode, "alpha": 0.85, "tol": tol,
+                   "accumulate": ("contributions as int64 round(C * 2^62), exact integer sums; "
+                                  "ranks FP64" if args.precision == "fp64" else
+                                  "FP32 contributions, TwoSum-compensated FP32 sums; FP64 "
+                                  "dead-end sum, L-inf and normalisation"),
                    "l2": "flushed by a 256 MiB write between steps (outside the events)",
                    "replicas": ws},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -480,9 +547,115 @@ def run_ours(args):
                  "apply_plus_df_ms_steps": step_ms, "wall_s": t_wall,
                  "nonconverged_steps": len(bad)},
     }
+    if ws == 1 and args.workload == "rmat24" and not args.no_extras:
+        # the other configurations of the metric, each at its full size with
+        # its own clocks and parity check (a failure is recorded, not fatal)
+        g.free()
+        del dev_batches, flush
+        torch.cuda.empty_cache()
+        extras = {}
+        for key, fn in (("rmat24_fp32", lambda: extra_single(dfpr, torch, dev, "rmat24", "fp32")),
+                        ("grid4096_fp32", lambda: extra_single(dfpr, torch, dev, "grid4096", "fp32")),
+                        ("many256_fp32", lambda: extra_many(dfpr, torch, dev)),
+                        ("serve8_fp64", lambda: extra_serve(dfpr, torch, dev))):
+            t0 = time.perf_counter()
+            try:
+                extras[key] = fn()
+            except Exception as e:  # noqa: BLE001 - recorded in the line
+                extras[key] = {"error": f"{type(e).__name__}: {e}"}
+            extras[key]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
+        line["extras"] = extras
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# compact measurements of the other configurations, added to the default line
+# --------------------------------------------------------------------------
+
+def extra_single(dfpr, torch, dev, wname, precision, steps=5, warmup=3, batch_frac=1e-4):
+    """One single-graph configuration at its full size: ms per batch (apply +
+    update, CUDA events, L2 flushed between steps), the persistent kernel's
+    algorithmic-byte rate, the work counters, clocks, and a parity check: Eq. 1
+    residuals at sampled vertices, evaluated with numpy from the exported graph
+    and ranks."""
+    spec = WORKLOADS[wname]
+    n, src, dst = make_graph(spec)
+    prec = dfpr.FP64 if precision == "fp64" else dfpr.FP32
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    g = dfpr.graph_load(n, src, dst, dfpr.default_config(precision=prec), stream=stream.cuda_stream)
+    m0 = g.info()["m"]
+    tol = 1e-10 if precision == "fp64" else 1e-7
+    dfpr.static_pagerank(g, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000.0, max_iter=1000))
+    b = max(1, int(round(batch_frac * m0)))
+    params = dfpr.default_params(tol=tol)
+    batches = [[torch.from_numpy(x).to(dev) for x in make_batch(spec, n, src, dst, b, 300 + i)]
+               for i in range(warmup + steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for i in range(warmup):
+        dfpr.apply_batch(g, *batches[i])
+        dfpr.df_pagerank(g, params)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms, stats = [], []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dfpr.apply_batch(g, *batches[warmup + k])
+        st = dfpr.df_pagerank(g, params)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(st.as_dict())
+    clk = clocks.stop()
+    s_r = 8 if precision == "fp64" else 4
+    kern = float(np.mean([x["ms"] for x in stats]))
+    byts = float(np.mean([algorithmic_bytes(x, s_r) for x in stats]))
+    peak, peak_kind = load_peaks()
+    R = dfpr.get_ranks(g)
+    in_off, in_idx = dfpr.get_csc(g)
+    res, res_rel, k = host_residual(R, in_off, in_idx)
+    g.free()
+    del flush
+    torch.cuda.empty_cache()
+    mean = lambda key: float(np.mean([x[key] for x in stats]))  # noqa: E731
+    return {
+        "workload": f"{wname}-batch{batch_frac:g}", "precision": precision, "n": n, "m": m0,
+        "batch_edges": b, "ms_per_batch": float(np.mean(ms)), "kernel_ms": kern,
+        "roofline": {"achieved": byts / (kern * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": byts / (kern * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
+        "work": {"processed": mean("processed"), "edges_gathered": mean("edges_gathered"),
+                 "expansions": mean("expansions"), "edges_marked": mean("edges_marked"),
+                 "affected": mean("affected")},
+        "nonconverged_steps": sum(x["status"] != dfpr.OK for x in stats),
+        "parity": {"check": "Eq. 1 residual at sampled vertices (numpy, FP64, exported graph)",
+                   "vertices": k, "max_abs": res, "max_rel": res_rel,
+                   "bound": "tau = 1e-10 absolute" if precision == "fp64"
+                   else "1e-6 relative"},
+        "clocks": clk,
+    }
+
+
+def extra_many(dfpr, torch, dev, graphs=256, steps=2, warmup=1, precision="fp32"):
+    """The many-graph configuration at N = 1: one persistent launch per step over
+    all graphs against each graph updated alone in turn (per-graph latency from
+    the step's start), with parity between the two forms and Eq. 1 residuals of
+    the set's ranks."""
+    a = argparse.Namespace(graphs=graphs, steps=steps, warmup=warmup, precision=precision,
+                           autotune=False, timeout_ms=60000.0)
+    return many_measure(a, quiet=True)
+
+
+def extra_serve(dfpr, torch, dev, requests=150, load=0.8):
+    """The serving configuration at one offered load (80 % of the measured
+    single-stream capacity)."""
+    a = argparse.Namespace(requests=requests, precision="fp64", timeout_ms=60000.0)
+    return serve_measure(a, loads=(load,), quiet=True)
 
 
 def pct(xs, q):
@@ -513,7 +686,7 @@ def gather_to_rank0(xs):
     return [x for part in got for x in part]
 
 
-def run_many(args):
+def many_measure(args, quiet=False):
     """Many graphs in one persistent launch per step (a set loaded with
     dfpr_graph_load_parts) against plain per-graph DF, one graph after another,
     on the same GPU. Per-graph latency of a step: from the step's start to the
@@ -522,11 +695,10 @@ def run_many(args):
 
     import paper_2407_19562_gb300 as dfpr
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
+    if ws > 1 and not (torch.distributed.is_available() and torch.distributed.is_initialized()):
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
+        torch.distributed.init_process_group("nccl")
+    elif ws == 1:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
@@ -568,7 +740,10 @@ def run_many(args):
         return out
 
     set_lat, single_lat, set_step, single_step, set_kernel, set_bytes = [], [], [], [], [], []
+    clocks = ClockSampler(torch.cuda.current_device())
     for step in range(total):
+        if step == args.warmup:
+            clocks.start()
         bl = batches_for(step)
         gb = [np.concatenate([b[k] + o for b, o in zip(bl, off)]).astype(np.int32) for k in range(4)]
         dev_gb = [torch.from_numpy(x).to(dev) for x in gb]
@@ -608,8 +783,12 @@ def run_many(args):
             single_step.append(lat1[-1])
             set_kernel.append(st.ms)
             set_bytes.append(algorithmic_bytes(st.as_dict(), 8 if prec == dfpr.FP64 else 4))
+    clk = clocks.stop()
     # both forms reach the same ranks (each graph's update is the same method)
     Rs = dfpr.get_ranks(s_set)
+    in_off, in_idx = dfpr.get_csc(s_set)
+    res, res_rel, nres = host_residual(Rs, in_off, in_idx, part_off=off)
+    res_rel = max_over_ranks(res_rel, dev)
     diff = max(float(np.max(np.abs(Rs[off[i]:off[i + 1]] - dfpr.get_ranks(g))))
                for i, g in enumerate(singles))
     # whole job: every rank's graphs, timed by the slowest rank
@@ -624,9 +803,10 @@ def run_many(args):
     achieved = bytes_total / (kernel_total * 1e-3) / 1e9 if kernel_total > 0 else 0.0
     set_lat, single_lat = gather_to_rank0(set_lat), gather_to_rank0(single_lat)
     m_total = gather_to_rank0([int(len(gsrc))])
-    if rank != 0:
-        torch.distributed.destroy_process_group()
-        return
+    s_set.free()
+    for g in singles:
+        g.free()
+    torch.cuda.empty_cache()
     line = {
         "metric": "many-graph DF: ms/step and per-graph p50/p99 latency (batched vs per-graph)",
         "value": set_total / args.steps, "unit": "ms/step", "n_gpus": ws, "steps": args.steps,
@@ -644,6 +824,11 @@ def run_many(args):
         "per_graph_sequential": {"ms_per_step": single_total / args.steps,
                                  "p50_ms": pct(single_lat, 50), "p99_ms": pct(single_lat, 99)},
         "max_abs_diff_batched_vs_alone": diff,
+        "parity": {"check": "Eq. 1 residual at sampled vertices of the set (numpy, FP64, "
+                            "each graph's own n)", "vertices": nres, "max_rel": res_rel,
+                   "bound": "1e-6 relative" if prec == dfpr.FP32 else "tau = 1e-10 absolute",
+                   "batched_vs_alone": diff},
+        "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "kernel": "k_worklist over the set (one launch per step)",
@@ -652,30 +837,47 @@ def run_many(args):
                    "autotuned": bool(args.autotune),
                    "trial_ms": [float(x) for x in tune_trials] if args.autotune else None},
     }
-    print(json.dumps(line), flush=True)
+    if not quiet and rank == 0:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def run_many(args):
+    many_measure(args)
+    ws, _, _ = dist_env()
     if ws > 1:
+        import torch
         torch.distributed.destroy_process_group()
 
 
-def run_serve(args):
+def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
     """Serving loop: 8 resident R-MAT graphs (scales 18,18,19,19,20,20,21,22,
     16 draws per vertex) receiving a Poisson stream of update batches, sizes
-    log-uniform in [10, 1e5] (80/20), graph uniform. The native server batches
-    every request admitted in a cycle into one persistent launch; the plain form
-    serves one request per cycle. Offered load: 50/80/95% of the measured
-    single-stream capacity (mean service time of requests served one by one)."""
+    log-uniform in [10, 1e5] (80/20), graph uniform. Three forms serve the same
+    stream from the same starting ranks:
+      continuous - dfpr_server over 8 units (one graph each, own stream and
+                   worker): a request is admitted as soon as its graph is idle
+                   and runs beside the other graphs' updates;
+      cycles     - dfpr_server over one set of the 8 graphs: every admitted
+                   request of a cycle in one persistent launch, new requests
+                   wait for the next cycle;
+      plain      - dfpr_apply_batch + dfpr_df_pagerank per request, one at a
+                   time in arrival order.
+    Offered load: a fraction of the single-stream capacity (mean service time
+    of requests served one at a time). Latency = completion - arrival (host
+    monotonic clock)."""
     import threading as th
 
     import torch
 
     import paper_2407_19562_gb300 as dfpr
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
+    if ws > 1 and not (torch.distributed.is_available() and torch.distributed.is_initialized()):
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
+        torch.distributed.init_process_group("nccl")
+    elif ws == 1:
         torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     scales = [18, 18, 19, 19, 20, 20, 21, 22]
     # the resident graphs shard across ranks; each rank serves the requests
     # to its own graphs, at the same fraction of its own measured capacity
@@ -694,9 +896,12 @@ def run_serve(args):
     prec = dfpr.FP64 if args.precision == "fp64" else dfpr.FP32
     tol = 1e-10 if args.precision == "fp64" else 1e-7
     cfg = dfpr.default_config(precision=prec)
-    gset = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=None)
-    st0 = dfpr.static_pagerank(gset, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
     params = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
+    # starting ranks: static PageRank of the set (untimed)
+    gset = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=None)
+    dfpr.static_pagerank(gset, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
+    R0 = dfpr.get_ranks(gset)
+    gset.free()
     u = workloads.uniform01(6000, 1, 3 * 7 * args.requests * ws + 256 * ws)
 
     def make_requests(k0, count):
@@ -712,66 +917,119 @@ def run_serve(args):
             reqs.append((local_of[gi], workloads.uniform_batch(n, b, 60000 + k0 + j, src, dst)))
         return reqs
 
-    def run_stream(reqs, gaps, slots):
-        if not reqs:
-            raise SystemExit("a rank drew no requests: raise --requests")
-        srv = dfpr.server_create(gset, params, max_slots=slots, mem_fraction=0.5)
-        ids = [None] * len(reqs)
-        t0 = time.perf_counter()
+    def load_units():
+        units = []
+        for k, (n, src, dst) in enumerate(graphs):
+            h = dfpr.graph_load(n, src, dst, cfg, stream=None)
+            dfpr.set_ranks(h, np.ascontiguousarray(R0[off[k]:off[k + 1]]))
+            units.append(h)
+        return units
 
-        def submitter():
+    def load_set():
+        h = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=None)
+        dfpr.set_ranks(h, R0)
+        return h
+
+    def final_ranks(form, held):
+        if form == "cycles":
+            R = dfpr.get_ranks(held)
+            return [R[off[k]:off[k + 1]].copy() for k in range(len(graphs))]
+        return [dfpr.get_ranks(h) for h in held]
+
+    def run_form(form, reqs, gaps):
+        held = load_set() if form == "cycles" else load_units()
+        lat, edges = [], sum(len(b[0]) + len(b[2]) for _, b in reqs)
+        t0 = time.perf_counter()
+        if form == "plain":
             t = t0
+            done = []
             for j, (gi, batch) in enumerate(reqs):
                 t += gaps[j]
                 d = t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                ids[j] = srv.submit(gi, *batch)
+                dfpr.apply_batch(held[gi], *batch)
+                st = dfpr.df_pagerank(held[gi], params)
+                done.append((t, time.perf_counter(), st.status))
+            lat = [(b - a) * 1e3 for a, b, _ in done]
+            span = done[-1][1] - t0
+            bad = sum(x[2] != dfpr.OK for x in done)
+            updates = len(reqs)
+        else:
+            # continuous: every launch capped at half a wave, so that two
+            # units' updates run side by side and a third starts as one ends
+            share = (5 * torch.cuda.get_device_properties(dev).multi_processor_count) // 2
+            srv = dfpr.server_create(held, params, max_slots=64, mem_fraction=0.5,
+                                     grid_share=share if form == "continuous" else 0)
+            ids = [None] * len(reqs)
 
-        thr = th.Thread(target=submitter)
-        thr.start()
-        thr.join()
-        infos = [srv.wait(r) for r in ids]
-        srv.destroy()
-        lat = [i.done_ms - i.submit_ms for i in infos]
-        span = (max(i.done_ms for i in infos) - min(i.submit_ms for i in infos)) / 1e3
-        edges = sum(len(b[0]) + len(b[2]) for _, b in reqs)
-        # whole job: latencies of every rank, rates summed over ranks
+            def submitter():
+                t = t0
+                for j, (gi, batch) in enumerate(reqs):
+                    t += gaps[j]
+                    d = t - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    ids[j] = srv.submit(gi, *batch)
+
+            thr = th.Thread(target=submitter)
+            thr.start()
+            thr.join()
+            infos = [srv.wait(r) for r in ids]
+            srv.destroy()
+            lat = [i.done_ms - i.submit_ms for i in infos]
+            span = (max(i.done_ms for i in infos) - min(i.submit_ms for i in infos)) / 1e3
+            bad = sum(i.status != dfpr.OK for i in infos)
+            updates = len({i.cycle for i in infos})
+        R = final_ranks(form, held)
+        for h in (held if isinstance(held, list) else [held]):
+            h.free()
         lat = gather_to_rank0(lat)
-        tot = gather_to_rank0([(edges, len(reqs), span, len({i.cycle for i in infos}),
-                                sum(i.status != dfpr.OK for i in infos))])
-        return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(np.mean(lat)),
-                "updates_per_s": sum(t[0] / t[2] for t in tot if t[2] > 0),
-                "requests_per_s": sum(t[1] / t[2] for t in tot if t[2] > 0),
-                "cycles": sum(t[3] for t in tot), "bad": sum(t[4] for t in tot)}
+        tot = gather_to_rank0([(edges, len(reqs), span, updates, bad)])
+        return R, {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(np.mean(lat)),
+                   "updates_per_s": sum(t[0] / t[2] for t in tot if t[2] > 0),
+                   "requests_per_s": sum(t[1] / t[2] for t in tot if t[2] > 0),
+                   "launches": sum(t[3] for t in tot), "bad": sum(t[4] for t in tot)}
 
     # single-stream capacity: requests served one at a time, back to back
     cal = make_requests(0, 40 * ws)
-    srv = dfpr.server_create(gset, params, max_slots=1)
+    units = load_units()
     svc = []
     for gi, batch in cal:
-        r = srv.wait(srv.submit(gi, *batch))
-        svc.append(r.done_ms - r.admit_ms)
-    srv.destroy()
+        t = time.perf_counter()
+        dfpr.apply_batch(units[gi], *batch)
+        dfpr.df_pagerank(units[gi], params)
+        svc.append((time.perf_counter() - t) * 1e3)
+    for h in units:
+        h.free()
     mean_svc = float(np.mean(svc))
     svc_all = gather_to_rank0([mean_svc])
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     points = []
     k = max(200, 120 * ws + 8)  # past the calibration draws
-    for load in (0.5, 0.8, 0.95):
-        # fresh batches for each form (a replayed batch would be all no-ops),
-        # same distribution and the same arrival times
-        reqs_b = make_requests(k, args.requests * ws)
-        reqs_p = make_requests(k + 3 * args.requests * ws, args.requests * ws)
-        k += 6 * args.requests * ws
+    for load in loads:
+        reqs = make_requests(k, args.requests * ws)
+        k += 3 * args.requests * ws
+        if not reqs:
+            raise SystemExit("a rank drew no requests: raise --requests")
         rate = load / (mean_svc / 1e3)
         rng = np.random.default_rng(int(load * 100) + 1000 * rank)
-        gaps = rng.exponential(1.0 / rate, size=len(reqs_b))
-        batched = run_stream(reqs_b, gaps, 64)
-        plain = run_stream(reqs_p[:len(reqs_b)], gaps, 1)
-        points.append({"load": load, "offered_req_per_s": rate, "batched": batched, "plain": plain})
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        out, ranks = {"load": load, "offered_req_per_s": rate}, {}
+        for form in ("continuous", "cycles", "plain"):
+            ranks[form], out[form] = run_form(form, reqs, gaps)
+        # every form applied the same requests in the same order per graph
+        diff = max(float(np.max(np.abs(a - b))) for f in ("continuous", "cycles")
+                   for a, b in zip(ranks[f], ranks["plain"]))
+        out["max_abs_diff_vs_plain"] = max_over_ranks(diff)
+        points.append(out)
+    clk = clocks.stop()
     line = {
-        "metric": "serving: per-batch p50/p99 latency (ms) and updates/s, batched vs one request per cycle",
-        "value": points[-1]["batched"]["p99_ms"], "unit": "ms (p99 at 95% load, batched)",
+        "metric": "serving: per-batch p50/p99 latency (ms) and updates/s; continuous units vs "
+                  "cycles vs plain per-batch calls",
+        "value": points[-1]["continuous"]["p99_ms"],
+        "unit": f"ms (p99 at {int(round(100 * loads[-1]))}% load, continuous)",
         "n_gpus": ws, "higher_is_better": False, "scaling": "weak",
         "dtype": "f64" if prec == dfpr.FP64 else "f32", "data": "synthetic",
         "config": {"workload": "serve8: R-MAT scales 18,18,19,19,20,20,21,22; Poisson arrivals; "
@@ -781,10 +1039,21 @@ def run_serve(args):
                                "at the load fraction of its own capacity",
                    "precision": args.precision},
         "points": points,
+        "parity": {"check": "final ranks of every graph, continuous and cycles against plain "
+                            "per-batch updates of the same requests",
+                   "bound": 1e-9 if prec == dfpr.FP64 else "1e-6 relative"},
+        "clocks": clk,
     }
-    if rank == 0:
+    if not quiet and rank == 0:
         print(json.dumps(line), flush=True)
+    return line
+
+
+def run_serve(args):
+    serve_measure(args)
+    ws, _, _ = dist_env()
     if ws > 1:
+        import torch
         torch.distributed.destroy_process_group()
 
 

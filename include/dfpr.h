@@ -116,7 +116,9 @@ typedef struct dfpr_params {
                           mode the cap is max_iter * n recomputations in total */
   int32_t mode;        /* DFPR_MODE_* */
   int32_t normalize;   /* 1: rescale ranks to sum 1 (FP64 sum) after convergence */
-  int32_t grid_ctas;   /* persistent grid size; 0 = one wave on every SM */
+  int32_t grid_ctas;   /* persistent grid size; 0 = the schedule's own: worklist about
+                          sqrt(n)/4 CTAs (at least 8, at most one wave on every SM),
+                          round at most n/2048, jacobi one wave */
   double timeout_ms;   /* wall-clock budget on the device; <= 0 means 60000 */
   /* Simulated faults (Sec. 5.1.6; experiments of Sec. 5.3 and 5.4). All 0 by
      default. A warp stands for one of the paper's threads; every draw comes
@@ -362,9 +364,9 @@ typedef struct dfpr_request_info {
 
 /* A server over k units (graphs or sets, distinct). Parts are numbered over
  * the units in order: unit 0's graphs first. grid_share > 0 caps every
- * launch at that many CTAs (when params->grid_ctas is 0), so that updates of
- * several units can be resident on the GPU together; 0 gives each launch a
- * full grid. EINVAL (k < 1, a NULL or repeated unit, max_slots < 1,
+ * worklist launch at that many CTAs (when params->grid_ctas is 0), so that
+ * updates of several units are resident on the GPU together; 0 leaves each
+ * launch its schedule's own grid. EINVAL (k < 1, a NULL or repeated unit, max_slots < 1,
  * mem_fraction outside (0, 1], grid_share < 0), EBUSY (a unit is in use),
  * ENOMEM. */
 dfpr_status dfpr_server_create_units(int32_t k, dfpr_graph* const* units, const dfpr_params* p,

@@ -1870,6 +1870,22 @@ int persistent_grid(dfpr_graph* g, const dfpr_params& p, const void* kernel) {
   return per_sm * g->sm_count;
 }
 
+// Grid of the worklist schedule: at most one wave, and about sqrt(n) / 4 CTAs
+// (at least 8). Every warp holds 32 vertices in flight; when the in-flight
+// set is a large share of the frontier, vertices are recomputed from inputs
+// that are about to change and are queued again. Measured on R-MAT graphs
+// with 16 draws per vertex, batch 1e-4 |E| (ms per update at a full wave of
+// 760 CTAs / at the grid this rule gives): scale 18, 18-23 / 12-16 (154
+// CTAs); scale 20, 30 / 22 (256); scale 22, 50 / 44-47 (512); scale 24 keeps
+// the full wave (112 ms; 141 ms at half of it).
+template <class P>
+int worklist_grid(dfpr_graph* g, const dfpr_params& p) {
+  const int full = persistent_grid(g, p, (const void*)k_worklist<P>);
+  if (p.grid_ctas > 0) return full;
+  const long long by_size = (long long)(0.25 * std::sqrt((double)g->n));
+  return (int)std::max<long long>(std::min<long long>(8, full), std::min<long long>(full, by_size));
+}
+
 // Grid of the round schedule. One CTA per 2048 vertices at most: warps move
 // to the next pass as soon as the current one's chunks are claimed, so the
 // more vertices are in flight at once, the more each pass computes from
@@ -1972,7 +1988,7 @@ dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr
   }
   if (g->nparts > 1)
     DFPR_CUDA(cudaMemsetAsync(g->part_done.p, 0, sizeof(unsigned long long) * g->nparts, s));
-  const int grid = persistent_grid(g, p, (const void*)k_worklist<P>);
+  const int grid = worklist_grid<P>(g, p);
   DFPR_CUDA(cudaEventRecord(e0, s));  // the stats time the persistent kernel alone
   set_fault_warps(a, grid);
   k_worklist<P><<<grid, kNT, 0, s>>>(a);
@@ -2219,7 +2235,7 @@ dfpr_status run_any(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stat
     }
   } guard{e0, e1};
   if (p.fault_crash_warps > 0) {  // checked before any device work
-    const int grid = p.mode == DFPR_MODE_WORKLIST ? persistent_grid(g, p, (const void*)k_worklist<P>)
+    const int grid = p.mode == DFPR_MODE_WORKLIST ? worklist_grid<P>(g, p)
                                                   : round_grid<P>(g, p);
     DFPR_REQUIRE((long long)p.fault_crash_warps < (long long)grid * kWPB, DFPR_EINVAL,
                  "fault_crash_warps must be below the number of warps of the launch");
@@ -2365,6 +2381,12 @@ void residual(dfpr_graph* g, double alpha, double* linf, double* linf_rel) {
   DFPR_CUDA(cudaStreamSynchronize(s));
   memcpy(linf, &b[0], sizeof(double));
   memcpy(linf_rel, &b[1], sizeof(double));
+}
+
+int default_worklist_grid(dfpr_graph* g, const dfpr_params& p) {
+  dfpr_params q = p;
+  q.grid_ctas = 0;
+  return g->cfg.precision == DFPR_FP64 ? worklist_grid<P64>(g, q) : worklist_grid<P32>(g, q);
 }
 
 dfpr_status run_iteration(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st) {

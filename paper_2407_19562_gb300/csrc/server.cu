@@ -177,7 +177,8 @@ void serve_unit(dfpr_server* s, Unit* u) {
       }
       for (auto& layer : layers) apply_layer(u, layer);
       dfpr_params p = s->p;
-      if (p.grid_ctas == 0 && s->grid_share > 0) p.grid_ctas = s->grid_share;
+      if (p.grid_ctas == 0 && s->grid_share > 0)
+        p.grid_ctas = std::min(default_worklist_grid(u->g, p), s->grid_share);
       dfpr_stats stats;
       st = run_update(u->g, &p, &stats, kRunDF);
     } catch (const Fail& f) {
