@@ -47,9 +47,14 @@ def parse():
     ap.add_argument("--graph", choices=["rmat24", "rmat20", "rmat24e4", "grid4096"], default="rmat24",
                     help="sweep: the graph")
     ap.add_argument("--requests", type=int, default=300, help="serve8: requests per load point")
+    ap.add_argument("--units", type=int, default=2,
+                    help="serve8: continuous form over this many units (sets of graphs)")
+    ap.add_argument("--share-div", type=int, default=2,
+                    help="serve8: continuous launches are capped at 1/share-div of a wave")
     ap.add_argument("--graphs", type=int, default=256, help="many256: number of graphs")
     ap.add_argument("--autotune", action="store_true",
-                    help="many256: pick the split thresholds with dfpr_autotune on the first step")
+                    help="many256: pick the set's schedule, grid and split thresholds with "
+                         "dfpr_autotune_plans on the first (warm-up) step")
     ap.add_argument("--batch-frac", type=float, default=1e-4)
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--mode", choices=["worklist", "round", "jacobi"], default="worklist")
@@ -156,13 +161,13 @@ def l2_bytes(dev) -> int:
 
 
 def algorithmic_bytes(st, s_r: int) -> float:
-    """Bytes the method must move for the counted work:
-    per recomputed vertex: in-row descriptor (16 B), own rank read, rank and
-    contribution writes (3 s_R), out-row descriptor for its degree (16 B);
-    per gathered in-edge: id (4 B) + contribution (s_R); per expansion: the
-    out-row descriptor (16 B); per marked out-edge: id (4 B) + flag word RMW
-    (4 B); per queue insertion: slot write + read (8 B)."""
-    return (st["processed"] * (32 + 3 * s_r) + st["edges_gathered"] * (4 + s_r)
+    """Bytes the method must move for the counted work, whatever the layout:
+    per recomputed vertex: in-row offset and degree (16 B), out-degree (4 B),
+    own rank read, rank and contribution writes (3 s_R); per gathered in-edge:
+    id (4 B) + contribution (s_R); per expansion: the out-row offset and degree
+    (16 B); per marked out-edge: id (4 B) + flag word RMW (4 B); per queue
+    insertion: slot write + read (8 B)."""
+    return (st["processed"] * (20 + 3 * s_r) + st["edges_gathered"] * (4 + s_r)
             + st["expansions"] * 16 + st["edges_marked"] * 8 + st["pushes"] * 8)
 
 
@@ -231,6 +236,33 @@ def measured_traffic(workload, precision, mode):
     if rec is None or rec[0] != kernel_source_hash():
         return None
     return rec[1]
+
+
+def random_line_ceiling(torch, dev, gib=4, count=1 << 26, reps=5):
+    """Random-access ceiling of the memory system: 8-byte gathers at uniformly
+    random positions of a gib-GiB array (far larger than L2), timed with CUDA
+    events (torch's index_select). Every gather costs one DRAM line fetch, so
+    the rate is the device's ceiling for scattered lines, the bound that the
+    DF kernel's contribution and state reads meet long before the copy
+    bandwidth."""
+    big = torch.zeros(gib << 27, dtype=torch.int64, device=dev)
+    idx = torch.randint(0, big.numel(), (count,), device=dev, dtype=torch.int64)
+    out = torch.empty(count, dtype=torch.int64, device=dev)
+    torch.index_select(big, 0, idx, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(reps):
+        e0.record()
+        torch.index_select(big, 0, idx, out=out)
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    del big, idx, out
+    torch.cuda.empty_cache()
+    rate = count / (best * 1e-3)
+    return {"lines_per_s": rate, "gb_s_at_64B_lines": rate * 64 / 1e9,
+            "how": f"index_select of {count} random int64 from a {gib} GiB array, best of {reps}"}
 
 
 def load_peaks():
@@ -472,6 +504,7 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     traffic = measured_traffic(f"{args.workload}-batch{args.batch_frac:g}", args.precision, args.mode)
     ws_bytes, l2 = working_set_bytes(n, m0, s_r), l2_bytes(dev)
+    ceiling = random_line_ceiling(torch, dev)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -534,7 +567,12 @@ def run_ours(args):
                      # a working set inside L2 never reaches HBM after the
                      # first touch: the HBM fraction is then low by design
                      "working_set_bytes": ws_bytes, "l2_bytes": l2,
-                     "fits_l2": bool(l2) and ws_bytes <= l2},
+                     "fits_l2": bool(l2) and ws_bytes <= l2,
+                     # scattered 64-byte DRAM lines: the kernel's DRAM traffic
+                     # in lines per second against the measured ceiling
+                     "random_line_ceiling": ceiling,
+                     "dram_lines_frac_of_ceiling": ((traffic / 64.0) / (float(np.mean(kern_ms)) * 1e-3)
+                                                    / ceiling["lines_per_s"] if traffic else None)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -647,14 +685,15 @@ def extra_many(dfpr, torch, dev, graphs=256, steps=2, warmup=1, precision="fp32"
     the step's start), with parity between the two forms and Eq. 1 residuals of
     the set's ranks."""
     a = argparse.Namespace(graphs=graphs, steps=steps, warmup=warmup, precision=precision,
-                           autotune=False, timeout_ms=60000.0)
+                           autotune=True, timeout_ms=60000.0)
     return many_measure(a, quiet=True)
 
 
 def extra_serve(dfpr, torch, dev, requests=150, load=0.8):
     """The serving configuration at one offered load (80 % of the measured
     single-stream capacity)."""
-    a = argparse.Namespace(requests=requests, precision="fp64", timeout_ms=60000.0)
+    a = argparse.Namespace(requests=requests, precision="fp64", timeout_ms=60000.0, units=2,
+                           share_div=2)
     return serve_measure(a, loads=(load,), quiet=True)
 
 
@@ -727,7 +766,8 @@ def many_measure(args, quiet=False):
         dfpr.set_ranks(g, np.ascontiguousarray(R0[off[i]:off[i + 1]]))
         singles.append(g)
     params = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
-    tune_trials = []
+    params_alone = dfpr.default_params(tol=tol, timeout_ms=args.timeout_ms)
+    tune_trials, tune_plans = [], []
     total = args.warmup + args.steps
     if args.autotune and args.warmup < 1:
         raise SystemExit("--autotune needs a warm-up step")
@@ -754,7 +794,7 @@ def many_measure(args, quiet=False):
         e0.record()
         dfpr.apply_batch(s_set, *dev_gb)
         if args.autotune and step == 0:  # a warm-up step: tunes, then applies the update
-            params, tune_trials, st = dfpr.autotune(s_set, params)
+            params, tune_plans, tune_trials, st = dfpr.autotune_plans(s_set, params)
         else:
             st = dfpr.df_pagerank(s_set, params)
         e1.record()
@@ -770,7 +810,7 @@ def many_measure(args, quiet=False):
         evs = []
         for i, g in enumerate(singles):
             dfpr.apply_batch(g, *dev_bl[i])
-            dfpr.df_pagerank(g, params)
+            dfpr.df_pagerank(g, params_alone)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record()
             evs.append(ev)
@@ -833,9 +873,11 @@ def many_measure(args, quiet=False):
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "kernel": "k_worklist over the set (one launch per step)",
                      "algorithmic_bytes_per_launch": bytes_total / args.steps},
-        "splits": {"gather_split": int(params.gather_split), "mark_split": int(params.mark_split),
-                   "autotuned": bool(args.autotune),
-                   "trial_ms": [float(x) for x in tune_trials] if args.autotune else None},
+        "plan": {"mode": ["worklist", "round", "jacobi"][int(params.mode)],
+                 "grid_ctas": int(params.grid_ctas), "gather_split": int(params.gather_split),
+                 "mark_split": int(params.mark_split), "autotuned": bool(args.autotune),
+                 "trials": ([{"plan": [int(x) for x in pl], "ms": float(t)}
+                             for pl, t in zip(tune_plans, tune_trials)] if args.autotune else None)},
     }
     if not quiet and rank == 0:
         print(json.dumps(line), flush=True)
@@ -855,9 +897,10 @@ def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
     16 draws per vertex) receiving a Poisson stream of update batches, sizes
     log-uniform in [10, 1e5] (80/20), graph uniform. Three forms serve the same
     stream from the same starting ranks:
-      continuous - dfpr_server over 8 units (one graph each, own stream and
-                   worker): a request is admitted as soon as its graph is idle
-                   and runs beside the other graphs' updates;
+      continuous - dfpr_server over --units units (sets of graphs balanced by
+                   edge draws, each with its own stream and worker): a
+                   request is admitted as soon as its unit is idle and runs
+                   beside the other units' updates;
       cycles     - dfpr_server over one set of the 8 graphs: every admitted
                    request of a cycle in one persistent launch, new requests
                    wait for the next cycle;
@@ -917,27 +960,41 @@ def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
             reqs.append((local_of[gi], workloads.uniform_batch(n, b, 60000 + k0 + j, src, dst)))
         return reqs
 
-    def load_units():
-        units = []
-        for k, (n, src, dst) in enumerate(graphs):
-            h = dfpr.graph_load(n, src, dst, cfg, stream=None)
-            dfpr.set_ranks(h, np.ascontiguousarray(R0[off[k]:off[k + 1]]))
+    def load_groups(k):
+        """The rank's graphs in k units (sets of graphs balanced by edge draws;
+        a unit of one graph is loaded alone). Returns the units, each graph's
+        part index in the server's numbering (units in order), and each
+        graph's (unit, vertex offset in the unit)."""
+        k = max(1, min(k, len(graphs)))
+        groups = assign_by_edges([len(g[1]) for g in graphs], k)
+        units, part_of, where = [], [0] * len(graphs), [None] * len(graphs)
+        base = 0
+        for grp in groups:
+            if len(grp) == 1:
+                i = grp[0]
+                n, src, dst = graphs[i]
+                h = dfpr.graph_load(n, src, dst, cfg, stream=None)
+                dfpr.set_ranks(h, np.ascontiguousarray(R0[off[i]:off[i + 1]]))
+                part_of[i], where[i] = base, (len(units), 0)
+            else:
+                o = np.cumsum([0] + [graphs[i][0] for i in grp])
+                us = np.concatenate([graphs[i][1] + o[j] for j, i in enumerate(grp)]).astype(np.int32)
+                ud = np.concatenate([graphs[i][2] + o[j] for j, i in enumerate(grp)]).astype(np.int32)
+                h = dfpr.graph_load_parts(o.astype(np.int32), us, ud, cfg, stream=None)
+                dfpr.set_ranks(h, np.concatenate([R0[off[i]:off[i + 1]] for i in grp]))
+                for j, i in enumerate(grp):
+                    part_of[i], where[i] = base + j, (len(units), int(o[j]))
             units.append(h)
-        return units
+            base += len(grp)
+        return units, part_of, where
 
-    def load_set():
-        h = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=None)
-        dfpr.set_ranks(h, R0)
-        return h
-
-    def final_ranks(form, held):
-        if form == "cycles":
-            R = dfpr.get_ranks(held)
-            return [R[off[k]:off[k + 1]].copy() for k in range(len(graphs))]
-        return [dfpr.get_ranks(h) for h in held]
+    def final_ranks(units, where):
+        Rs = [dfpr.get_ranks(h) for h in units]
+        return [Rs[u][o:o + graphs[i][0]].copy() for i, (u, o) in enumerate(where)]
 
     def run_form(form, reqs, gaps):
-        held = load_set() if form == "cycles" else load_units()
+        k = {"cycles": 1, "plain": len(graphs)}.get(form, getattr(args, "units", 2))
+        held, part_of, where = load_groups(k)
         lat, edges = [], sum(len(b[0]) + len(b[2]) for _, b in reqs)
         t0 = time.perf_counter()
         if form == "plain":
@@ -948,17 +1005,18 @@ def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
                 d = t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                dfpr.apply_batch(held[gi], *batch)
-                st = dfpr.df_pagerank(held[gi], params)
+                dfpr.apply_batch(held[where[gi][0]], *batch)
+                st = dfpr.df_pagerank(held[where[gi][0]], params)
                 done.append((t, time.perf_counter(), st.status))
             lat = [(b - a) * 1e3 for a, b, _ in done]
             span = done[-1][1] - t0
             bad = sum(x[2] != dfpr.OK for x in done)
             updates = len(reqs)
         else:
-            # continuous: every launch capped at half a wave, so that two
-            # units' updates run side by side and a third starts as one ends
-            share = (5 * torch.cuda.get_device_properties(dev).multi_processor_count) // 2
+            # continuous: every launch capped at a share of a wave (half by
+            # default), so that units' updates run side by side
+            share = (5 * torch.cuda.get_device_properties(dev).multi_processor_count) // \
+                max(1, getattr(args, "share_div", 2))
             srv = dfpr.server_create(held, params, max_slots=64, mem_fraction=0.5,
                                      grid_share=share if form == "continuous" else 0)
             ids = [None] * len(reqs)
@@ -970,7 +1028,7 @@ def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
                     d = t - time.perf_counter()
                     if d > 0:
                         time.sleep(d)
-                    ids[j] = srv.submit(gi, *batch)
+                    ids[j] = srv.submit(part_of[gi], *batch)
 
             thr = th.Thread(target=submitter)
             thr.start()
@@ -981,8 +1039,8 @@ def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
             span = (max(i.done_ms for i in infos) - min(i.submit_ms for i in infos)) / 1e3
             bad = sum(i.status != dfpr.OK for i in infos)
             updates = len({i.cycle for i in infos})
-        R = final_ranks(form, held)
-        for h in (held if isinstance(held, list) else [held]):
+        R = final_ranks(held, where)
+        for h in held:
             h.free()
         lat = gather_to_rank0(lat)
         tot = gather_to_rank0([(edges, len(reqs), span, updates, bad)])
@@ -993,12 +1051,12 @@ def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
 
     # single-stream capacity: requests served one at a time, back to back
     cal = make_requests(0, 40 * ws)
-    units = load_units()
+    units, _, where = load_groups(len(graphs))
     svc = []
     for gi, batch in cal:
         t = time.perf_counter()
-        dfpr.apply_batch(units[gi], *batch)
-        dfpr.df_pagerank(units[gi], params)
+        dfpr.apply_batch(units[where[gi][0]], *batch)
+        dfpr.df_pagerank(units[where[gi][0]], params)
         svc.append((time.perf_counter() - t) * 1e3)
     for h in units:
         h.free()
@@ -1035,6 +1093,8 @@ def serve_measure(args, loads=(0.5, 0.8, 0.95), quiet=False):
         "config": {"workload": "serve8: R-MAT scales 18,18,19,19,20,20,21,22; Poisson arrivals; "
                                "batch sizes log-uniform [10,1e5], 80/20",
                    "requests_per_point": args.requests, "mean_service_ms": svc_all,
+                   "continuous_grid_share": f"1/{max(1, getattr(args, 'share_div', 2))} of a wave",
+                   "continuous_units": getattr(args, "units", 2),
                    "sharding": "graphs to ranks by greedy balance of edge draws; each rank "
                                "at the load fraction of its own capacity",
                    "precision": args.precision},

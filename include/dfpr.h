@@ -409,6 +409,54 @@ dfpr_status dfpr_set_allocator(dfpr_alloc_fn alloc, dfpr_free_fn free_fn, void* 
 const char* dfpr_last_error(void);
 
 /*
+ * CUDA-graph replay of the DF update (no counterpart in the paper; for the
+ * many-graph step of a set, whose update is one persistent launch). With
+ * enable = 1, dfpr_df_pagerank on the worklist schedule runs its device work
+ * (marking items of the pending change set, control block, per-vertex
+ * records, the persistent kernel, ranks back) as one replay of a CUDA graph
+ * that the library captures on the graph's stream at the first such call and
+ * again whenever a buffer, the grid or a parameter it depends on changes; the
+ * pending counts reach the replay through pinned host memory, so a replay
+ * serves any batch. The stream must not be the legacy default stream (such
+ * calls run eagerly), and the first call captures, so it must not itself be
+ * made while the stream is being captured. dfpr_apply_batch stays eager: its
+ * allocation sizes depend on the batch. Results and stats are those of the
+ * eager path; stats.ms is the persistent kernel's time. enable = 0 frees the
+ * graph. Errors: EINVAL (NULL graph), EBUSY, ECUDA.
+ */
+dfpr_status dfpr_graph_set_capture(dfpr_graph* g, int32_t enable);
+
+/* Captures made and replays launched so far by dfpr_graph_set_capture's
+ * path (host int64 each, may be NULL). EINVAL for a NULL graph. */
+dfpr_status dfpr_graph_capture_info(const dfpr_graph* g, int64_t* captures, int64_t* replays);
+
+/*
+ * Autotuner over plans (no counterpart in the paper): a plan is the schedule
+ * and the tile choices of an update, four int32: mode (DFPR_MODE_*), grid_ctas
+ * (0: the schedule's own), gather_split and mark_split (0: the defaults; they
+ * bound the degree classes: rows gathered or marked by one warp against rows
+ * cut into tokens). Like dfpr_autotune it runs the pending update once per
+ * plan from the same ranks, contributions and pending change set, times each
+ * whole call with CUDA events, restores that state once more and runs the
+ * fastest plan, which stays applied; cost: plans + 1 updates.
+ * plans: host, 4 * n_plans int32, or NULL for the built-in set: the worklist
+ * schedule at the graph's own grid, at half of it and at a full wave (size
+ * classes), at its own grid with split pairs (2048, 2048) and (16384, 16384)
+ * (degree classes; pairs below the graph's minimum split are left out), and
+ * the jacobi schedule (DF_BB, Alg. 1); teleport graphs: the jacobi schedule
+ * alone. At most 8 built-in plans.
+ * p: in, the parameters of every trial; out, the same with the chosen plan's
+ * four fields. Outputs (host, may be NULL): *n_run the plans timed;
+ * plans_run[4 * n_run] those plans; trial_ms[n_run] their times (INFINITY
+ * for a trial that did not converge); *stats the final update's counters.
+ * Returns the final update's status. Errors: EINVAL (NULL graph or p, no
+ * pending change, an invalid plan), EBUSY, ENOMEM, ECUDA.
+ */
+dfpr_status dfpr_autotune_plans(dfpr_graph* g, dfpr_params* p, int32_t n_plans,
+                                const int32_t* plans, int32_t* n_run, int32_t* plans_run,
+                                double* trial_ms, dfpr_stats* stats);
+
+/*
  * FP64 residual of the stored ranks (the L-inf test of Alg. 1, taken on the
  * final state rather than on consecutive iterates): for every vertex,
  * r'(v) = (1 - alpha)/n + alpha * sum over in-edges (u, v) of R[u] / |out(u)|

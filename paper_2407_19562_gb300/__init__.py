@@ -25,8 +25,8 @@ __all__ = [
     "kernel_launches",
     "default_config", "default_params", "graph_load", "graph_free", "graph_info",
     "graph_set_stream", "apply_batch", "df_pagerank", "nd_pagerank", "static_pagerank",
-    "get_ranks", "set_ranks", "residual", "get_csr", "get_csc", "initial_affected", "set_allocator",
-    "graph_load_parts", "get_part_times", "Server", "RequestInfo", "server_create",
+    "get_ranks", "set_ranks", "residual", "set_capture", "capture_info", "get_csr", "get_csc", "initial_affected", "set_allocator",
+    "graph_load_parts", "get_part_times", "autotune", "autotune_plans", "Server", "RequestInfo", "server_create",
     "use_torch_allocator", "OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "EBUSY",
     "FP64", "FP32", "SELF_LOOPS", "TELEPORT", "WORKLIST", "ROUND", "JACOBI",
 ]
@@ -148,6 +148,10 @@ def load():
             "dfpr_last_error": (ctypes.c_char_p, []),
             "dfpr_version": (i32, []),
             "dfpr_kernel_launches": (i64, []),
+            "dfpr_autotune_plans": (st, [vp, ctypes.POINTER(Params), i32, vp, ctypes.POINTER(i32),
+                                         vp, vp, ctypes.POINTER(Stats)]),
+            "dfpr_graph_set_capture": (st, [vp, i32]),
+            "dfpr_graph_capture_info": (st, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "dfpr_residual": (st, [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
             "dfpr_static_pagerank_noalloc": (st, [i32, vp, vp, vp, ctypes.c_double,
@@ -292,6 +296,9 @@ class Graph:
     def autotune(self, *a, **k):
         return autotune(self, *a, **k)
 
+    def autotune_plans(self, *a, **k):
+        return autotune_plans(self, *a, **k)
+
     def static_pagerank(self, *a, **k):
         return static_pagerank(self, *a, **k)
 
@@ -303,6 +310,12 @@ class Graph:
 
     def residual(self, *a, **k):
         return residual(self, *a, **k)
+
+    def set_capture(self, *a, **k):
+        return set_capture(self, *a, **k)
+
+    def capture_info(self):
+        return capture_info(self)
 
     def get_csr(self, *a, **k):
         return get_csr(self, *a, **k)
@@ -434,6 +447,34 @@ def autotune(g: Graph, params: Params | None = None, candidates=None):
     return p, trials, st
 
 
+def autotune_plans(g: Graph, params: Params | None = None, plans=None):
+    """dfpr_autotune_plans: times the pending update under each plan (mode,
+    grid_ctas, gather_split, mark_split) and leaves it applied with the
+    fastest. plans None: the library's built-in set. Returns (tuned Params,
+    the plans timed as an (k, 4) int32 array, their times in ms, Stats of the
+    final update)."""
+    p = Params.from_buffer_copy(params if params is not None else default_params())
+    if plans is None:
+        k, arr = 0, None
+    else:
+        arr = np.ascontiguousarray(np.asarray(plans, np.int32).reshape(-1, 4))
+        k = len(arr)
+    cap = max(k, 8)
+    run = ctypes.c_int32()
+    plans_run = np.zeros((cap, 4), np.int32)
+    trials = np.zeros(cap, np.float64)
+    st = Stats()
+    rc = load().dfpr_autotune_plans(g.handle, ctypes.byref(p), k,
+                                    arr.ctypes.data if arr is not None else None,
+                                    ctypes.byref(run), plans_run.ctypes.data, trials.ctypes.data,
+                                    ctypes.byref(st))
+    if rc not in (OK, ENOTCONV, ETIMEOUT):
+        _check(rc, "autotune_plans")
+    st.status = rc
+    r = run.value
+    return p, plans_run[:r].copy(), trials[:r].copy(), st
+
+
 def nd_pagerank(g: Graph, params: Params | None = None) -> Stats:
     """dfpr_nd_pagerank: naive-dynamic update from the current ranks."""
     return _run(load().dfpr_nd_pagerank, "nd_pagerank", g, params)
@@ -452,6 +493,19 @@ def get_ranks(g: Graph, out=None):
     p, _, dev = _ptr(out, np.float64, g.n, "out")
     _check(load().dfpr_get_ranks(g.handle, p, dev), "get_ranks")
     return out
+
+
+def set_capture(g: Graph, enable: bool = True):
+    """dfpr_graph_set_capture: replay the worklist DF update's device work from a
+    CUDA graph (captured on the first call), or go back to eager launches."""
+    _check(load().dfpr_graph_set_capture(g.handle, 1 if enable else 0), "set_capture")
+
+
+def capture_info(g: Graph):
+    """dfpr_graph_capture_info -> (captures made, replays launched)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().dfpr_graph_capture_info(g.handle, ctypes.byref(a), ctypes.byref(b)), "capture_info")
+    return a.value, b.value
 
 
 def residual(g: Graph, alpha: float = 0.85):

@@ -396,6 +396,10 @@ dfpr_status dfpr_graph_free(dfpr_graph* g) {
   unsigned long long* pinned = g->pinned;
   std::vector<cudaStream_t> retired;
   retired.swap(g->retired_streams);
+  if (g->cap_exec) cudaGraphExecDestroy(g->cap_exec);
+  for (cudaEvent_t e : g->cap_ev)
+    if (e) cudaEventDestroy(e);
+  if (g->cap_host) cudaFreeHost(g->cap_host);
   // device arrays are released by their destructors, with the streams they
   // were allocated on still alive (an installed allocator may use them)
   delete g;
@@ -428,6 +432,35 @@ dfpr_status dfpr_graph_set_stream(dfpr_graph* g, void* cuda_stream) {
   }
   return DFPR_OK;
   API_END
+}
+
+dfpr_status dfpr_graph_set_capture(dfpr_graph* g, int32_t enable) {
+  if (!g) {
+    set_error("graph is NULL");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  g->capture = enable != 0;
+  if (!g->capture && g->cap_exec) {
+    DFPR_CUDA(cudaStreamSynchronize(g->stream));
+    DFPR_CUDA(cudaGraphExecDestroy(g->cap_exec));
+    g->cap_exec = nullptr;
+    g->cap_key.clear();
+  }
+  return DFPR_OK;
+  API_END
+}
+
+dfpr_status dfpr_graph_capture_info(const dfpr_graph* g, int64_t* captures, int64_t* replays) {
+  if (!g) {
+    set_error("graph is NULL");
+    return DFPR_EINVAL;
+  }
+  if (captures) *captures = g->cap_captures;
+  if (replays) *replays = g->cap_replays;
+  return DFPR_OK;
 }
 
 dfpr_status dfpr_graph_info(const dfpr_graph* g, int32_t* n, int64_t* m, int32_t* device) {
@@ -487,6 +520,99 @@ dfpr_status dfpr_df_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* st
   API_END
 }
 
+namespace {
+
+// Runs the pending update once per plan (mode, grid_ctas, gather_split,
+// mark_split), each time from the same ranks, contributions and pending
+// change set, timing the whole call with CUDA events; then restores that
+// state once more and runs the fastest plan, which stays applied.
+dfpr_status autotune_plans(dfpr_graph* g, dfpr_params* p, int32_t k, const int32_t* plans,
+                           double* trial_ms, dfpr_stats* stats) {
+  DFPR_REQUIRE(g->pend.n_src > 0 || g->pend.n_dst > 0, DFPR_EINVAL,
+               "dfpr_autotune: no pending changes to time the candidates on");
+  auto plan_params = [&](int32_t i) {
+    dfpr_params q = *p;
+    q.mode = plans[4 * i];
+    q.grid_ctas = plans[4 * i + 1];
+    q.gather_split = plans[4 * i + 2];
+    q.mark_split = plans[4 * i + 3];
+    return q;
+  };
+  for (int32_t i = 0; i < k; ++i) {
+    const dfpr_params q = plan_params(i);
+    check_params(q);
+    if (g->cfg.dead_end == DFPR_TELEPORT)
+      DFPR_REQUIRE(q.mode == DFPR_MODE_JACOBI, DFPR_EINVAL,
+                   "dfpr_autotune: teleport graphs run the jacobi schedule only");
+  }
+  cudaStream_t s = g->stream;
+  const long long n_src = g->pend.n_src, n_dst = g->pend.n_dst;
+  const bool fp64 = g->cfg.precision == DFPR_FP64;
+  const size_t r_bytes = (fp64 ? sizeof(double) : sizeof(float)) * (size_t)g->n;
+  const size_t c_bytes = (fp64 ? sizeof(long long) : sizeof(float)) * (size_t)g->n;
+  // the jacobi schedule swaps its two vectors: look the current ones up each time
+  auto vectors = [&](void** R, void** C) {
+    *R = fp64 ? (void*)g->R64.p : (void*)g->R32.p;
+    *C = fp64 ? (void*)g->C64.p : (void*)g->C32.p;
+  };
+  DevArray<unsigned char> snap;  // the ranks and contributions every trial starts from
+  snap.reset(r_bytes + c_bytes, s);
+  void *R, *C;
+  vectors(&R, &C);
+  DFPR_CUDA(cudaMemcpyAsync(snap.p, R, r_bytes, cudaMemcpyDeviceToDevice, s));
+  DFPR_CUDA(cudaMemcpyAsync(snap.p + r_bytes, C, c_bytes, cudaMemcpyDeviceToDevice, s));
+  const double d_before = g->d_before;
+  const bool d_valid = g->d_before_valid;
+  auto restore = [&]() {
+    void *R2, *C2;
+    vectors(&R2, &C2);
+    DFPR_CUDA(cudaMemcpyAsync(R2, snap.p, r_bytes, cudaMemcpyDeviceToDevice, s));
+    DFPR_CUDA(cudaMemcpyAsync(C2, snap.p + r_bytes, c_bytes, cudaMemcpyDeviceToDevice, s));
+    g->pend.n_src = n_src;  // the pending arrays are left intact by an update
+    g->pend.n_dst = n_dst;
+    g->d_before = d_before;
+    g->d_before_valid = d_valid;
+  };
+  cudaEvent_t e0, e1;
+  DFPR_CUDA(cudaEventCreate(&e0));
+  DFPR_CUDA(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } guard{e0, e1};
+  double best = INFINITY;
+  int32_t bi = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    if (i > 0) restore();
+    dfpr_params q = plan_params(i);
+    dfpr_stats st;
+    DFPR_CUDA(cudaEventRecord(e0, s));
+    const dfpr_status r = run_update(g, &q, &st, kRunDF);
+    DFPR_CUDA(cudaEventRecord(e1, s));
+    DFPR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DFPR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    const double t = r == DFPR_OK ? (double)ms : INFINITY;
+    if (trial_ms) trial_ms[i] = t;
+    if (t < best) {
+      best = t;
+      bi = i;
+    }
+  }
+  restore();
+  *p = plan_params(bi);
+  dfpr_stats st;
+  const dfpr_status r = run_update(g, p, &st, kRunDF);
+  if (stats) *stats = st;
+  DFPR_CUDA(cudaStreamSynchronize(s));
+  return r;
+}
+
+}  // namespace
+
 dfpr_status dfpr_autotune(dfpr_graph* g, dfpr_params* p, int32_t n_candidates,
                           const int32_t* candidates, double* trial_ms, dfpr_stats* stats) {
   static const int32_t kDefaultPairs[8] = {2048, 2048, 4096, 8192, 8192, 8192, 16384, 16384};
@@ -501,56 +627,60 @@ dfpr_status dfpr_autotune(dfpr_graph* g, dfpr_params* p, int32_t n_candidates,
   DeviceGuard dg(g->device);
   DFPR_REQUIRE(p->mode != DFPR_MODE_JACOBI, DFPR_EINVAL,
                "dfpr_autotune: the split thresholds apply to the worklist and round schedules");
-  DFPR_REQUIRE(g->pend.n_src > 0 || g->pend.n_dst > 0, DFPR_EINVAL,
-               "dfpr_autotune: no pending changes to time the candidates on");
+  std::vector<int32_t> plans((size_t)4 * k);
   for (int32_t i = 0; i < k; ++i) {
-    dfpr_params q = *p;
-    q.gather_split = cand[2 * i];
-    q.mark_split = cand[2 * i + 1];
-    check_params(q);
+    plans[4 * i] = p->mode;
+    plans[4 * i + 1] = p->grid_ctas;
+    plans[4 * i + 2] = cand[2 * i];
+    plans[4 * i + 3] = cand[2 * i + 1];
   }
-  cudaStream_t s = g->stream;
-  const long long n_src = g->pend.n_src, n_dst = g->pend.n_dst;
-  const bool fp64 = g->cfg.precision == DFPR_FP64;
-  const size_t rb = sizeof(double) * (size_t)g->n, cb = sizeof(long long) * (size_t)g->n;
-  const size_t rb32 = sizeof(float) * (size_t)g->n;
-  void* R = fp64 ? (void*)g->R64.p : (void*)g->R32.p;
-  void* C = fp64 ? (void*)g->C64.p : (void*)g->C32.p;
-  const size_t r_bytes = fp64 ? rb : rb32, c_bytes = fp64 ? cb : rb32;
-  DevArray<unsigned char> snap;  // the ranks and contributions every trial starts from
-  snap.reset(r_bytes + c_bytes, s);
-  DFPR_CUDA(cudaMemcpyAsync(snap.p, R, r_bytes, cudaMemcpyDeviceToDevice, s));
-  DFPR_CUDA(cudaMemcpyAsync(snap.p + r_bytes, C, c_bytes, cudaMemcpyDeviceToDevice, s));
-  auto restore = [&]() {
-    DFPR_CUDA(cudaMemcpyAsync(R, snap.p, r_bytes, cudaMemcpyDeviceToDevice, s));
-    DFPR_CUDA(cudaMemcpyAsync(C, snap.p + r_bytes, c_bytes, cudaMemcpyDeviceToDevice, s));
-    g->pend.n_src = n_src;  // the pending arrays are left intact by an update
-    g->pend.n_dst = n_dst;
-  };
-  double best = INFINITY;
-  int32_t bi = 0;
-  for (int32_t i = 0; i < k; ++i) {
-    if (i > 0) restore();
+  return autotune_plans(g, p, k, plans.data(), trial_ms, stats);
+  API_END
+}
+
+dfpr_status dfpr_autotune_plans(dfpr_graph* g, dfpr_params* p, int32_t n_plans,
+                                const int32_t* plans, int32_t* n_run, int32_t* plans_run,
+                                double* trial_ms, dfpr_stats* stats) {
+  if (n_run) *n_run = 0;
+  if (!g || !p || (plans && n_plans < 1)) {
+    set_error("dfpr_autotune_plans: need a graph, parameters and at least one plan");
+    return DFPR_EINVAL;
+  }
+  API_BEGIN
+  BusyGuard bg(g);
+  DeviceGuard dg(g->device);
+  std::vector<int32_t> def;
+  if (!plans) {
+    // size classes (worklist grid: the graph's own, half of it, a full wave),
+    // degree classes (split thresholds), and the barrier-based schedule
+    const int rule = default_worklist_grid(g, *p);
     dfpr_params q = *p;
-    q.gather_split = cand[2 * i];
-    q.mark_split = cand[2 * i + 1];
-    dfpr_stats st;
-    const dfpr_status r = run_update(g, &q, &st, kRunDF);
-    const double ms = r == DFPR_OK ? st.ms : INFINITY;
-    if (trial_ms) trial_ms[i] = ms;
-    if (ms < best) {
-      best = ms;
-      bi = i;
+    q.grid_ctas = 0;
+    q.mode = DFPR_MODE_JACOBI;
+    const int full = full_worklist_grid(g, *p);
+    if (g->cfg.dead_end == DFPR_TELEPORT) {
+      def = {DFPR_MODE_JACOBI, 0, 0, 0};
+    } else {
+      def = {DFPR_MODE_WORKLIST, rule, 0, 0,
+             DFPR_MODE_WORKLIST, std::max(8, rule / 2), 0, 0,
+             DFPR_MODE_WORKLIST, std::max(rule, full), 0, 0,
+             DFPR_MODE_WORKLIST, rule, 2048, 2048,
+             DFPR_MODE_WORKLIST, rule, 16384, 16384,
+             DFPR_MODE_JACOBI, 0, 0, 0};
+      // splits below the graph's minimum are left out
+      const long long min_split = std::max<long long>(256, (g->m + (1ll << 20) - 1) >> 20);
+      std::vector<int32_t> keep;
+      for (size_t i = 0; i < def.size(); i += 4)
+        if ((def[i + 2] == 0 || def[i + 2] >= min_split) && (def[i + 3] == 0 || def[i + 3] >= min_split))
+          keep.insert(keep.end(), def.begin() + i, def.begin() + i + 4);
+      def.swap(keep);
     }
+    plans = def.data();
+    n_plans = (int32_t)(def.size() / 4);
   }
-  restore();
-  p->gather_split = cand[2 * bi];
-  p->mark_split = cand[2 * bi + 1];
-  dfpr_stats st;
-  const dfpr_status r = run_update(g, p, &st, kRunDF);
-  if (stats) *stats = st;
-  DFPR_CUDA(cudaStreamSynchronize(s));
-  return r;
+  if (n_run) *n_run = n_plans;
+  if (plans_run) std::copy(plans, plans + 4 * n_plans, plans_run);
+  return autotune_plans(g, p, n_plans, plans, trial_ms, stats);
   API_END
 }
 

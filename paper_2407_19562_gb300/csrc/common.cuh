@@ -106,21 +106,20 @@ struct Scratch {
 // Graph layout
 // ---------------------------------------------------------------------------
 
-// One row of CSR or CSC: edges[off .. off + deg) hold the row, sorted; the
-// slot reserves cap >= deg entries so that batches update it in place.
-// Per-vertex worklist record: X = the rank at the vertex's last expansion,
-// ep = the epoch (call) in which X was written; X is meaningful only when
-// ep is the current call's epoch.
-struct __align__(16) XE64 {
-  double x;
-  uint32_t ep;
-  uint32_t pad;
-};
-struct __align__(8) XE32 {
-  float x;
-  uint32_t ep;
+// Per-vertex record of one worklist call (built at its start, ranks copied
+// back at its end): the rank, the rank at the last expansion, the in-row as
+// offset << 25 | degree, the out-degree and a flag word (bit 0: recomputed in
+// this call). 32 bytes, one sector, so a recomputation reads its vertex's
+// state in one random access.
+struct __align__(32) VRec {
+  unsigned long long a;   // FP64: rank bits; FP32: rank bits | x bits << 32
+  unsigned long long b;   // FP64: x bits;    FP32: out-degree | flags << 32
+  unsigned long long in;  // in-row offset << 25 | in-degree
+  unsigned long long c;   // FP64: out-degree | flags << 32; FP32: unused
 };
 
+// One row of CSR or CSC: edges[off .. off + deg) hold the row, sorted; the
+// slot reserves cap >= deg entries so that batches update it in place.
 struct __align__(16) RowDesc {
   long long off;
   int deg;
@@ -164,6 +163,7 @@ struct DfCtl {
   HotI64 favail;      //   free slots
   unsigned long long n_src_items;  // marking items over out-rows of sources
   unsigned long long n_items;      // all marking items
+  long long n_mark_dst;            // deletion targets to mark
   unsigned int status;             // 0, or the dfpr_status that stopped the workers
   unsigned int abort;              // 1: workers stop
   unsigned long long edges, expansions, edges_marked, pushes, affected;
@@ -231,14 +231,10 @@ struct dfpr_graph {
   dfpr::DevArray<double> R64;              // rank
   dfpr::DevArray<long long> C64;           // contribution R/outdeg, fixed point 2^-62
   dfpr::DevArray<float> R32, C32;
-  // worklist: rank at the last expansion and the epoch (call) that wrote it,
-  // one record per vertex so that both come in one load
-  dfpr::DevArray<dfpr::XE64> XE64;
-  dfpr::DevArray<dfpr::XE32> XE32;
+  dfpr::DevArray<dfpr::VRec> vrec;        // worklist: per-vertex records of the running call
   dfpr::DevArray<double> R64b;             // second vectors of the Jacobi schedule
   dfpr::DevArray<long long> C64b;
   dfpr::DevArray<float> R32b, C32b;
-  uint32_t epoch = 0;                     // the current call's epoch
   dfpr::DevArray<uint32_t> state;         // 2 bits per vertex: bit0 queued, bit1 running
   dfpr::DevArray<int32_t> queue;          // qcap slots, -1 when empty
   unsigned long long qcap = 0;
@@ -273,4 +269,14 @@ struct dfpr_graph {
                                               // destroyed with the graph
   int sm_count = 0;
   int max_ctas = 0;
+  // CUDA-graph replay of the DF update's device work (dfpr_graph_set_capture)
+  bool capture = false;
+  cudaGraphExec_t cap_exec = nullptr;
+  std::vector<unsigned char> cap_key;       // what the captured launches depend on
+  cudaEvent_t cap_ev[2] = {nullptr, nullptr};
+  unsigned long long* cap_host = nullptr;   // pinned: pending counts read at replay
+  dfpr::DevArray<long long> cap_dev;        // 2: the same counts on the device
+  dfpr::Scratch cap_scratch;                // marking items and their scan, capture only
+  long long cap_launches = 0;               // kernels in the captured graph
+  long long cap_captures = 0, cap_replays = 0;
 };

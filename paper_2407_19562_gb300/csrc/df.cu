@@ -107,17 +107,36 @@ struct P64 {
   static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
   static __device__ __forceinline__ contrib load_c(const contrib* p) { return __ldcg(p); }
   static __device__ __forceinline__ acc shfl_xor(acc a, int d) { return __shfl_xor_sync(kFull, a, d); }
-  using xe = XE64;
-  static __device__ __forceinline__ void load_xe(const xe* p, val& x, uint32_t& ep) {
-    const longlong2 b = __ldcg(reinterpret_cast<const longlong2*>(p));
-    x = __longlong_as_double(b.x);
-    ep = (uint32_t)(b.y & 0xffffffffll);
+  // per-vertex record: {rank, x} | {in-row, out-degree | flags << 32}
+  static __device__ __forceinline__ void load_rec(const VRec* p, val& r, val& x, long long& ioff,
+                                                  int& ideg, int& od, unsigned& fl) {
+    const longlong2 u = __ldcg(reinterpret_cast<const longlong2*>(p));
+    const longlong2 w = __ldcg(reinterpret_cast<const longlong2*>(p) + 1);
+    r = __longlong_as_double(u.x);
+    x = __longlong_as_double(u.y);
+    ioff = (long long)((unsigned long long)w.x >> 25);
+    ideg = (int)(w.x & 0x1ffffffll);
+    od = (int)(w.y & 0xffffffffll);
+    fl = (unsigned)((unsigned long long)w.y >> 32);
   }
-  static __device__ __forceinline__ void store_xe(xe* p, val x, uint32_t ep) {
-    longlong2 b;
-    b.x = __double_as_longlong(x);
-    b.y = (long long)ep;
-    *reinterpret_cast<longlong2*>(p) = b;
+  static __device__ __forceinline__ void init_rec(VRec* p, val r, long long ioff, int ideg, int od) {
+    longlong2 u, w;
+    u.x = __double_as_longlong(r);
+    u.y = __double_as_longlong(r);
+    w.x = (long long)(((unsigned long long)ioff << 25) | (unsigned long long)ideg);
+    w.y = (long long)(unsigned)od;
+    reinterpret_cast<longlong2*>(p)[0] = u;
+    reinterpret_cast<longlong2*>(p)[1] = w;
+  }
+  static __device__ __forceinline__ void store_rx(VRec* p, val r, val x) {
+    longlong2 u;
+    u.x = __double_as_longlong(r);
+    u.y = __double_as_longlong(x);
+    *reinterpret_cast<longlong2*>(p) = u;
+  }
+  static __device__ __forceinline__ void set_fresh(VRec* p) { reinterpret_cast<unsigned*>(p)[7] = 1u; }
+  static __device__ __forceinline__ val rec_rank(const VRec* p) {
+    return __longlong_as_double(*reinterpret_cast<const long long*>(p));
   }
   // heavy-gather jobs: partial sums meet in one 64-bit word (exact integer adds)
   static __device__ __forceinline__ void job_add(unsigned long long* p, acc x) {
@@ -152,14 +171,29 @@ struct P32 {
   }
   static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
   static __device__ __forceinline__ contrib load_c(const contrib* p) { return __ldcg(p); }
-  using xe = XE32;
-  static __device__ __forceinline__ void load_xe(const xe* p, val& x, uint32_t& ep) {
-    const uint2 b = __ldcg(reinterpret_cast<const uint2*>(p));
-    x = __uint_as_float(b.x);
-    ep = b.y;
+  // per-vertex record: {rank, x, out-degree, flags} | {in-row, unused}
+  static __device__ __forceinline__ void load_rec(const VRec* p, val& r, val& x, long long& ioff,
+                                                  int& ideg, int& od, unsigned& fl) {
+    const uint4 u = __ldcg(reinterpret_cast<const uint4*>(p));
+    const unsigned long long in = __ldcg(reinterpret_cast<const unsigned long long*>(p) + 2);
+    r = __uint_as_float(u.x);
+    x = __uint_as_float(u.y);
+    od = (int)u.z;
+    fl = u.w;
+    ioff = (long long)(in >> 25);
+    ideg = (int)(in & 0x1ffffffull);
   }
-  static __device__ __forceinline__ void store_xe(xe* p, val x, uint32_t ep) {
-    *reinterpret_cast<uint2*>(p) = make_uint2(__float_as_uint(x), ep);
+  static __device__ __forceinline__ void init_rec(VRec* p, val r, long long ioff, int ideg, int od) {
+    reinterpret_cast<uint4*>(p)[0] = make_uint4(__float_as_uint(r), __float_as_uint(r), (unsigned)od, 0u);
+    reinterpret_cast<unsigned long long*>(p)[2] = ((unsigned long long)ioff << 25) | (unsigned long long)ideg;
+    reinterpret_cast<unsigned long long*>(p)[3] = 0ull;
+  }
+  static __device__ __forceinline__ void store_rx(VRec* p, val r, val x) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(__float_as_uint(r), __float_as_uint(x));
+  }
+  static __device__ __forceinline__ void set_fresh(VRec* p) { reinterpret_cast<unsigned*>(p)[3] = 1u; }
+  static __device__ __forceinline__ val rec_rank(const VRec* p) {
+    return __uint_as_float(*reinterpret_cast<const unsigned*>(p));
   }
   static __device__ __forceinline__ acc shfl_xor(acc a, int d) {
     return {__shfl_xor_sync(kFull, a.s, d), __shfl_xor_sync(kFull, a.c, d)};
@@ -198,8 +232,7 @@ struct Args {
   const int32_t* __restrict__ out_edges;
   typename P::val* R;
   typename P::contrib* C;
-  typename P::xe* XE;
-  uint32_t epoch;
+  VRec* rec;
   uint32_t* state;
   int32_t* queue;
   unsigned long long qmask;
@@ -747,10 +780,11 @@ __device__ void do_mark_item(const Args<P>& a, long long item, int lane, WarpSta
     if (lane == 0) st.c[kStMarked] += (unsigned long long)max(0ll, end - beg);
   } else {
     const long long j = (item - n_src_items) * 32 + lane;
-    const bool valid = j < a.n_mark_dst;
+    const long long n_mark_dst = a.ctl->n_mark_dst;
+    const bool valid = j < n_mark_dst;
     const int t = valid ? a.mark_dst[j] : 0;
     mark(t, valid);
-    if (lane == 0) st.c[kStMarked] += (unsigned long long)min(32ll, a.n_mark_dst - (item - n_src_items) * 32);
+    if (lane == 0) st.c[kStMarked] += (unsigned long long)min(32ll, n_mark_dst - (item - n_src_items) * 32);
   }
 }
 
@@ -797,34 +831,29 @@ __device__ __forceinline__ void note_done(const Args<P>& a, int v, int lane) {
 
 constexpr double kDriftFactor = 10.0;
 
-// Eq. 1 epilogue of one recomputed vertex v (lane-local): new rank r from the
-// gathered sum; Delta r against the stored rank; the rank at the last
-// expansion decides whether v marks its out-neighbours; the state's queued
-// bit decides re-queueing. Writes R, C, X and the epoch tag.
+// Eq. 1 epilogue of one recomputed vertex v on the per-vertex record: new
+// rank r from the gathered sum; Delta r against the record's rank; the rank
+// at the last expansion (initialised to the rank at the call's start) decides
+// whether v marks its out-neighbours. Writes the record's rank and x, the
+// recomputed flag, and C.
 template <class P>
-__device__ __forceinline__ void vertex_epilogue(const Args<P>& a, int v, double sum,
-                                                typename P::val r_old, uint32_t e_tag,
-                                                typename P::val x_prev, int od, double dangling,
-                                                bool& expand, bool& requeue, bool& fresh,
-                                                WarpStats& st) {
+__device__ __forceinline__ void vertex_epilogue_rec(const Args<P>& a, int v, double sum,
+                                                    typename P::val r_old, typename P::val x0,
+                                                    unsigned fl, int od, double dangling,
+                                                    bool& expand, bool& requeue, bool& fresh,
+                                                    WarpStats& st) {
   double s2 = sum;
   if (a.teleport) s2 += dangling / (double)a.n;
   const typename P::val r = (typename P::val)(base_of(a, v) + a.alpha * s2);
-  fresh = e_tag != a.epoch;
-  const typename P::val x0 = fresh ? r_old : x_prev;
+  fresh = (fl & 1u) == 0u;
   const double dr = fabs((double)r - (double)r_old);
-  a.R[v] = r;
   a.C[v] = contrib_of(r, od);
   const double thr_f = frontier_thr<P>(a.tol_f, r);
   const double thr = P::relative ? a.tol * fabs((double)r) : a.tol;
-  // FP64: the paper's rule (this recomputation moved r by more than tau_f),
-  // plus a bound on what dependants can miss without Alg. 2's repeated
-  // passes: also expand once r has drifted by more than kDriftFactor * tau_f
-  // since the last expansion. FP32: the drift rule alone (its relative
-  // tolerance needs every sub-threshold change accounted for).
   const double drift = fabs((double)r - (double)x0);
   expand = P::relative ? drift > thr_f : (dr > thr_f || drift > kDriftFactor * thr_f);
-  P::store_xe(a.XE + v, expand ? r : x0, a.epoch);
+  P::store_rx(a.rec + v, r, expand ? r : x0);
+  if (fresh) P::set_fresh(a.rec + v);
   requeue = dr > thr;
   st.max_change = fmax(st.max_change, dr);
 }
@@ -907,14 +936,14 @@ __device__ int run_gather_token(const Args<P>& a, unsigned slot, unsigned chunk,
   orow.deg = 0;
   if (vv >= 0) {
     const double sum = P::job_total(ld_volatile(a.job_sum + slot));
-    const typename P::val r_old = P::load(a.R + vv);
-    uint32_t e_tag;
-    typename P::val x_prev;
-    P::load_xe(a.XE + vv, x_prev, e_tag);
-    orow = load_row(a.out_rows + vv);
+    typename P::val r_old, x_prev;
+    long long ioff;
+    int ideg, od;
+    unsigned fl;
+    P::load_rec(a.rec + vv, r_old, x_prev, ioff, ideg, od, fl);
     const double dangling = a.teleport ? a.ctl->dsum : 0.0;
-    vertex_epilogue(a, vv, sum, r_old, e_tag, x_prev, orow.deg, dangling, expand, requeue, fresh,
-                    st);
+    vertex_epilogue_rec(a, vv, sum, r_old, x_prev, fl, od, dangling, expand, requeue, fresh, st);
+    if (expand) orow = load_row(a.out_rows + vv);
     free_job(a, (int)slot);
     st.c[kStAffected] += fresh ? 1ull : 0ull;  // lane 0 only
     st.c[kStExpansions] += expand ? 1ull : 0ull;
@@ -1084,12 +1113,18 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       return;  // crash-stop holding claimed vertices (Sec. 5.4)
     __threadfence();  // state change before reading neighbours' contributions
 
+    // the vertex's record: rank, x, in-row, out-degree, flags in one sector
+    typename P::val r_old = 0, x_prev = 0;
+    long long ioff = 0;
+    int ideg = 0, od = 0;
+    unsigned fl = 0;
+    if (v >= 0) P::load_rec(a.rec + v, r_old, x_prev, ioff, ideg, od, fl);
     // Heavy in-rows become jobs of gather tokens that any warp can take; the
     // vertex stays running (and keeps its pending unit) until its last chunk.
     {
       int nch = 0, slot = -1;
       if (v >= 0) {
-        const int din = load_row(a.in_rows + v).deg;
+        const int din = ideg;
         if (din > a.gather_split) {
           slot = alloc_job(a);
           if (slot >= 0) {
@@ -1110,23 +1145,18 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     }
     phase_mark(1);
 
-    // per-vertex loads issued before the gather so they overlap it
-    typename P::val r_old = 0, x_prev = 0;
-    uint32_t e_tag = 0;
+    const typename P::acc acc = gather_row(a, v >= 0 ? ideg : 0, ioff, lane, s_excl[w], s_off[w],
+                                           s_acc[w], st);
+    const double dangling = a.teleport ? ctl->dsum : 0.0;
+    bool expand = false, requeue = false, fresh = false;
     RowDesc orow;
     orow.off = 0;
     orow.deg = 0;
     if (v >= 0) {
-      r_old = P::load(a.R + v);
-      P::load_xe(a.XE + v, x_prev, e_tag);
-      orow = load_row(a.out_rows + v);
+      vertex_epilogue_rec(a, v, P::total(acc), r_old, x_prev, fl, od, dangling, expand, requeue,
+                          fresh, st);
+      if (expand) orow = load_row(a.out_rows + v);  // the out-row's offset: expansions only
     }
-    const typename P::acc acc = gather(a, v, lane, s_excl[w], s_off[w], s_acc[w], st);
-    const double dangling = a.teleport ? ctl->dsum : 0.0;
-    bool expand = false, requeue = false, fresh = false;
-    if (v >= 0)
-      vertex_epilogue(a, v, P::total(acc), r_old, e_tag, x_prev, orow.deg, dangling, expand,
-                      requeue, fresh, st);
     stats_count(st, kStAffected, fresh, lane);
     stats_count(st, kStExpansions, expand, lane);
     phase_mark(2);
@@ -1594,15 +1624,33 @@ __global__ void k_mark_chunks(const int32_t* __restrict__ src, long long ns,
   }
 }
 
+// k_mark_chunks over a capacity: entries at or past the device count *ns are 0
+// (a replayed launch reads the current count).
+__global__ void k_mark_chunks_cap(const int32_t* __restrict__ src, long long cap,
+                                  const long long* __restrict__ ns,
+                                  const RowDesc* __restrict__ out_rows, long long* cnt) {
+  const long long n = *ns;
+  GRID_STRIDE(i, cap) {
+    long long c = 0;
+    if (i < n) {
+      const long long d = out_rows[src[i]].deg;
+      c = d > 0 ? (d + kMarkChunk - 1) / kMarkChunk : 1;
+    }
+    cnt[i] = c;
+  }
+}
+
 __global__ void k_init_ctl(DfCtl* c, const long long* n_src_items_dev, long long n_mark_dst,
                            long long work_cap, long long seeded, int count_items_pending,
-                           int jobs) {
+                           int jobs, const long long* n_mark_dst_dev = nullptr) {
   const unsigned long long nsi = n_src_items_dev ? (unsigned long long)*n_src_items_dev : 0ull;
+  if (n_mark_dst_dev) n_mark_dst = *n_mark_dst_dev;
   const unsigned long long items = nsi + (unsigned long long)((n_mark_dst + 31) / 32);
   DfCtl z;
   memset(&z, 0, sizeof z);
   z.n_src_items = nsi;
   z.n_items = items;
+  z.n_mark_dst = n_mark_dst;
   z.pending.v = (count_items_pending ? (long long)items : 0) + seeded;
   z.tail.v = (unsigned long long)seeded;
   z.avail.v = seeded;
@@ -1627,6 +1675,23 @@ __global__ void k_seed_all(int32_t n, uint32_t* state, int32_t* queue) {
       state[i >> 4] = rem >= 16 ? 0x55555555u : (uint32_t)((1ull << (2 * rem)) - 1) & 0x55555555u;
     }
   }
+}
+
+// Per-vertex records of a worklist call from the ranks and row descriptors.
+template <class P>
+__global__ void k_build_rec(int32_t n, const RowDesc* __restrict__ in_rows,
+                            const RowDesc* __restrict__ out_rows,
+                            const typename P::val* __restrict__ R, VRec* rec) {
+  GRID_STRIDE(v, n) {
+    const RowDesc ir = load_row(in_rows + v);
+    P::init_rec(rec + v, R[v], ir.off, ir.deg, out_rows[v].deg);
+  }
+}
+
+// Ranks back from the records after a worklist call.
+template <class P>
+__global__ void k_rec_back(int32_t n, const VRec* __restrict__ rec, typename P::val* R) {
+  GRID_STRIDE(v, n) R[v] = P::rec_rank(rec + v);
 }
 
 template <class T>
@@ -1791,7 +1856,6 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   a.in_edges = g->in.edges.p;
   a.out_rows = g->out.rows.p;
   a.out_edges = g->out.edges.p;
-  a.epoch = g->epoch;
   a.state = g->state.p;
   a.queue = g->queue.p;
   a.qmask = g->qcap - 1;
@@ -1852,13 +1916,13 @@ template <>
 void set_vectors<P64>(dfpr_graph* g, Args<P64>& a) {
   a.R = g->R64.p;
   a.C = g->C64.p;
-  a.XE = g->XE64.p;
+  a.rec = g->vrec.p;
 }
 template <>
 void set_vectors<P32>(dfpr_graph* g, Args<P32>& a) {
   a.R = g->R32.p;
   a.C = g->C32.p;
-  a.XE = g->XE32.p;
+  a.rec = g->vrec.p;
 }
 
 int persistent_grid(dfpr_graph* g, const dfpr_params& p, const void* kernel) {
@@ -1957,43 +2021,161 @@ void reset_worklist_state(dfpr_graph* g) {
   DFPR_LAUNCHED();
 }
 
+// Enqueues the device work of a DF update on the worklist schedule for a
+// replayable CUDA graph: marking items over the capacity of the pending change
+// set (the counts are read on the device, from a word the graph's first node
+// copies from pinned host memory at every replay), the control block, the
+// per-vertex records, the persistent kernel between two events, and the ranks
+// copied back. Nothing here allocates or reads back.
+template <class P>
+void enqueue_captured_update(dfpr_graph* g, Args<P>& a, long long capn, long long* cnt,
+                             long long* off, long long work_cap, int grid) {
+  cudaStream_t s = g->stream;
+  DFPR_CUDA(cudaMemcpyAsync(g->cap_dev.p, g->cap_host, 2 * sizeof(long long),
+                            cudaMemcpyHostToDevice, s));
+  k_mark_chunks_cap<<<grid_small(capn), kNT, 0, s>>>(g->pend.src.p, capn, g->cap_dev.p,
+                                                     g->out.rows.p, cnt);
+  DFPR_LAUNCHED();
+  scan_exclusive_i64(cnt, off, capn, off + capn, g->cap_scratch, s);
+  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, off + capn, 0, work_cap, 0, 1, g->jcap, g->cap_dev.p + 1);
+  DFPR_LAUNCHED();
+  k_init_jobs<<<grid_small(g->jcap), kNT, 0, s>>>(g->job_ring.p, g->jcap);
+  DFPR_LAUNCHED();
+  if (g->nparts > 1)
+    DFPR_CUDA(cudaMemsetAsync(g->part_done.p, 0, sizeof(unsigned long long) * g->nparts, s));
+  k_build_rec<P><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->in.rows.p, g->out.rows.p, a.R, a.rec);
+  DFPR_LAUNCHED();
+  // external records: the replay records the events (a plain record inside a
+  // capture only orders the captured work)
+  DFPR_CUDA(cudaEventRecordWithFlags(g->cap_ev[0], s, cudaEventRecordExternal));
+  k_worklist<P><<<grid, kNT, 0, s>>>(a);
+  DFPR_LAUNCHED();
+  DFPR_CUDA(cudaEventRecordWithFlags(g->cap_ev[1], s, cudaEventRecordExternal));
+  k_rec_back<P><<<grid_small(g->n), kNT, 0, s>>>(g->n, a.rec, a.R);
+  DFPR_LAUNCHED();
+}
+
+// The DF update's device work replayed from a CUDA graph (captured on first
+// use, and again whenever a buffer, the grid or a parameter it was captured
+// with changes). Returns the persistent kernel's time in *kernel_ms.
+template <class P>
+void run_captured_update(dfpr_graph* g, const dfpr_params& p, Args<P>& a, float* kernel_ms) {
+  cudaStream_t s = g->stream;
+  const long long capn = std::max<long long>(1, (long long)g->pend.src.count);
+  long long* cnt = g->cap_scratch.get<long long>(0, (size_t)capn + 1, s);
+  long long* off = g->cap_scratch.get<long long>(1, (size_t)capn + 1, s);
+  // sizes the scan's level buffer outside the capture (no allocation may
+  // happen inside it); the values are recomputed at every replay
+  scan_exclusive_i64(cnt, off, capn, off + capn, g->cap_scratch, s);
+  if (g->cap_dev.count < 2) g->cap_dev.reset(2, s);
+  if (!g->cap_host) DFPR_CUDA(cudaMallocHost(&g->cap_host, 2 * sizeof(unsigned long long)));
+  for (int i = 0; i < 2; ++i)
+    if (!g->cap_ev[i]) DFPR_CUDA(cudaEventCreate(&g->cap_ev[i]));
+  if (g->vrec.count < (size_t)g->n) g->vrec.reset(g->n, s);
+  a.rec = g->vrec.p;
+  a.mark_src = g->pend.src.p;
+  a.mark_choff = off;
+  a.n_mark_src = capn;  // padded items hold no chunks
+  a.mark_dst = g->pend.dst.p;
+  a.n_mark_dst = 0;     // read from the control block
+  const int grid = worklist_grid<P>(g, p);
+  set_fault_warps(a, grid);
+  const long long work_cap = (long long)p.max_iter * (long long)g->n;
+  // what the captured launches depend on
+  std::vector<unsigned char> key(sizeof a);
+  memcpy(key.data(), &a, sizeof a);
+  const uintptr_t extra[] = {(uintptr_t)capn, (uintptr_t)cnt, (uintptr_t)off,
+                             (uintptr_t)g->cap_scratch.buf[kSlotScanSums].p,
+                             (uintptr_t)grid, (uintptr_t)g->part_done.p, (uintptr_t)g->nparts,
+                             (uintptr_t)work_cap, (uintptr_t)g->pend.dst.p,
+                             (uintptr_t)(g->cfg.precision), (uintptr_t)s};
+  key.insert(key.end(), (const unsigned char*)extra, (const unsigned char*)extra + sizeof extra);
+  if (!g->cap_exec || key != g->cap_key) {
+    if (g->cap_exec) {
+      DFPR_CUDA(cudaGraphExecDestroy(g->cap_exec));
+      g->cap_exec = nullptr;
+    }
+    g->cap_host[0] = g->cap_host[1] = 0;
+    const long long l0 = g_launches.load();
+    DFPR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+      enqueue_captured_update<P>(g, a, capn, cnt, off, work_cap, grid);
+    } catch (...) {
+      cudaStreamEndCapture(s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      throw;
+    }
+    DFPR_CUDA(cudaStreamEndCapture(s, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&g->cap_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    DFPR_CUDA(ie);
+    g->cap_launches = g_launches.load() - l0;
+    g_launches.fetch_add(-g->cap_launches);  // counted at every replay instead
+    g->cap_key.swap(key);
+    ++g->cap_captures;
+  }
+  g->cap_host[0] = (unsigned long long)g->pend.n_src;
+  g->cap_host[1] = (unsigned long long)g->pend.n_dst;
+  DFPR_CUDA(cudaGraphLaunch(g->cap_exec, s));
+  g_launches.fetch_add(g->cap_launches);
+  ++g->cap_replays;
+  DFPR_CUDA(cudaEventSynchronize(g->cap_ev[1]));
+  DFPR_CUDA(cudaEventElapsedTime(kernel_ms, g->cap_ev[0], g->cap_ev[1]));
+}
+
 template <class P>
 dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stats* st,
-                         cudaEvent_t e0, cudaEvent_t e1, bool mark_only) {
+                         cudaEvent_t e0, cudaEvent_t e1, bool mark_only, float* kernel_ms = nullptr) {
   cudaStream_t s = g->stream;
   Args<P> a = make_args<P>(g, p);
   set_vectors<P>(g, a);
   a.mark_only = mark_only ? 1 : 0;
-  long long* nsi = nullptr;
-  long long seeded = 0;
-  if (kind == kRunDF) {
-    nsi = prepare_marking<P>(g, a);
+  if (g->capture && kind == kRunDF && !mark_only && !a.teleport && s != nullptr && kernel_ms) {
+    run_captured_update<P>(g, p, a, kernel_ms);
   } else {
-    seeded = g->n;
-  }
-  const long long work_cap = (long long)p.max_iter * (long long)g->n;
-  k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, work_cap, seeded, 1, g->jcap);
-  DFPR_LAUNCHED();
-  k_init_jobs<<<grid_small(g->jcap), kNT, 0, s>>>(g->job_ring.p, g->jcap);
-  DFPR_LAUNCHED();
-  if (seeded) {
-    k_seed_all<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p, g->queue.p);
+    long long* nsi = nullptr;
+    long long seeded = 0;
+    if (kind == kRunDF) {
+      nsi = prepare_marking<P>(g, a);
+    } else {
+      seeded = g->n;
+    }
+    const long long work_cap = (long long)p.max_iter * (long long)g->n;
+    k_init_ctl<<<1, 1, 0, s>>>(g->ctl.p, nsi, kind == kRunDF ? g->pend.n_dst : 0, work_cap, seeded, 1, g->jcap);
     DFPR_LAUNCHED();
-  }
-  if (a.teleport) {
-    // the dead-end mass enters every vertex: computed once per call here
-    DFPR_CUDA(cudaMemsetAsync(&g->ctl.p->dsum, 0, sizeof(double), s));
-    k_dangling<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, a.R, &g->ctl.p->dsum);
+    k_init_jobs<<<grid_small(g->jcap), kNT, 0, s>>>(g->job_ring.p, g->jcap);
     DFPR_LAUNCHED();
+    if (seeded) {
+      k_seed_all<<<grid_small(g->n), kNT, 0, s>>>(g->n, g->state.p, g->queue.p);
+      DFPR_LAUNCHED();
+    }
+    if (a.teleport) {
+      // the dead-end mass enters every vertex: computed once per call here
+      DFPR_CUDA(cudaMemsetAsync(&g->ctl.p->dsum, 0, sizeof(double), s));
+      k_dangling<typename P::val><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->out.rows.p, a.R, &g->ctl.p->dsum);
+      DFPR_LAUNCHED();
+    }
+    if (g->nparts > 1)
+      DFPR_CUDA(cudaMemsetAsync(g->part_done.p, 0, sizeof(unsigned long long) * g->nparts, s));
+    const int grid = worklist_grid<P>(g, p);
+    if (!mark_only) {
+      if (g->vrec.count < (size_t)g->n) g->vrec.reset(g->n, s);
+      a.rec = g->vrec.p;
+      k_build_rec<P><<<grid_small(g->n), kNT, 0, s>>>(g->n, g->in.rows.p, g->out.rows.p, a.R, a.rec);
+      DFPR_LAUNCHED();
+    }
+    DFPR_CUDA(cudaEventRecord(e0, s));  // the stats time the persistent kernel alone
+    set_fault_warps(a, grid);
+    k_worklist<P><<<grid, kNT, 0, s>>>(a);
+    DFPR_LAUNCHED();
+    DFPR_CUDA(cudaEventRecord(e1, s));
+    if (!mark_only) {
+      k_rec_back<P><<<grid_small(g->n), kNT, 0, s>>>(g->n, a.rec, a.R);
+      DFPR_LAUNCHED();
+    }
   }
-  if (g->nparts > 1)
-    DFPR_CUDA(cudaMemsetAsync(g->part_done.p, 0, sizeof(unsigned long long) * g->nparts, s));
-  const int grid = worklist_grid<P>(g, p);
-  DFPR_CUDA(cudaEventRecord(e0, s));  // the stats time the persistent kernel alone
-  set_fault_warps(a, grid);
-  k_worklist<P><<<grid, kNT, 0, s>>>(a);
-  DFPR_LAUNCHED();
-  DFPR_CUDA(cudaEventRecord(e1, s));
   CtlHost h = read_ctl(g);
   if (st) fill_stats(h.c, st);
   if (g->nparts > 1 && !mark_only) {
@@ -2241,22 +2423,17 @@ dfpr_status run_any(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_stat
                  "fault_crash_warps must be below the number of warps of the launch");
   }
   if (kind == kRunStatic) reset_ranks(g);
-  g->epoch += 1;
-  if (g->epoch == 0) {  // wrapped: clear epochs so that no vertex looks current
-    if (g->cfg.precision == DFPR_FP64)
-      DFPR_CUDA(cudaMemsetAsync(g->XE64.p, 0, sizeof(XE64) * g->n, s));
-    else
-      DFPR_CUDA(cudaMemsetAsync(g->XE32.p, 0, sizeof(XE32) * g->n, s));
-    g->epoch = 1;
-  }
   dfpr_status r;
-  if (p.mode == DFPR_MODE_WORKLIST) r = run_worklist<P>(g, p, kind, st, e0, e1, false);
+  float kernel_ms = -1.f;  // set when the update ran from a captured CUDA graph
+  if (p.mode == DFPR_MODE_WORKLIST) r = run_worklist<P>(g, p, kind, st, e0, e1, false, &kernel_ms);
   else if (p.mode == DFPR_MODE_ROUND) r = run_round<P>(g, p, kind, st, e0, e1);
   else r = run_jacobi<P>(g, p, kind, st, e0, e1);
   if (p.normalize && r == DFPR_OK) normalize_ranks<P>(g);
-  float ms = 0.f;
-  DFPR_CUDA(cudaEventSynchronize(e1));
-  DFPR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  float ms = kernel_ms;
+  if (ms < 0.f) {
+    DFPR_CUDA(cudaEventSynchronize(e1));
+    DFPR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  }
   if (st) {
     st->ms = ms;
     st->status = r;
@@ -2275,15 +2452,10 @@ void alloc_iteration_state(dfpr_graph* g) {
   if (g->cfg.precision == DFPR_FP64) {
     g->R64.reset(n, s);
     g->C64.reset(n, s);
-    g->XE64.reset(n, s);
-    DFPR_CUDA(cudaMemsetAsync(g->XE64.p, 0, sizeof(XE64) * n, s));
   } else {
     g->R32.reset(n, s);
     g->C32.reset(n, s);
-    g->XE32.reset(n, s);
-    DFPR_CUDA(cudaMemsetAsync(g->XE32.p, 0, sizeof(XE32) * n, s));
   }
-  g->epoch = 0;
   g->state.reset(((size_t)n + 15) / 16, s);
   DFPR_CUDA(cudaMemsetAsync(g->state.p, 0, sizeof(uint32_t) * g->state.count, s));
   unsigned long long q = 1024;
@@ -2381,6 +2553,13 @@ void residual(dfpr_graph* g, double alpha, double* linf, double* linf_rel) {
   DFPR_CUDA(cudaStreamSynchronize(s));
   memcpy(linf, &b[0], sizeof(double));
   memcpy(linf_rel, &b[1], sizeof(double));
+}
+
+int full_worklist_grid(dfpr_graph* g, const dfpr_params& p) {
+  dfpr_params q = p;
+  q.grid_ctas = 0;
+  return g->cfg.precision == DFPR_FP64 ? persistent_grid(g, q, (const void*)k_worklist<P64>)
+                                       : persistent_grid(g, q, (const void*)k_worklist<P32>);
 }
 
 int default_worklist_grid(dfpr_graph* g, const dfpr_params& p) {

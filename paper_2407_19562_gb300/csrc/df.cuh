@@ -15,8 +15,10 @@ dfpr_status run_iteration(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfp
 // dfpr_nd_pagerank, dfpr_static_pagerank; the caller holds the graph).
 dfpr_status run_update(dfpr_graph* g, const dfpr_params* p, dfpr_stats* st, RunKind kind);
 
-// CTAs of the worklist schedule's own grid for g (params' grid_ctas ignored).
+// CTAs of the worklist schedule's own grid for g, and of one full wave
+// (params' grid_ctas ignored).
 int default_worklist_grid(dfpr_graph* g, const dfpr_params& p);
+int full_worklist_grid(dfpr_graph* g, const dfpr_params& p);
 
 // Initial marking only: affected flags (device, n bytes) and their count.
 void initial_affected(dfpr_graph* g, uint8_t* affected_dev, long long* count);

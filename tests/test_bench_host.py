@@ -37,7 +37,7 @@ def test_baseline_entry_scales_the_sample():
 def test_algorithmic_bytes_per_work_unit():
     b = load_bench()
     one = dict(processed=0, edges_gathered=0, expansions=0, edges_marked=0, pushes=0)
-    per = {"processed": (56, 44), "edges_gathered": (12, 8), "expansions": (16, 16),
+    per = {"processed": (44, 32), "edges_gathered": (12, 8), "expansions": (16, 16),
            "edges_marked": (8, 8), "pushes": (8, 8)}
     for k, (b64, b32) in per.items():
         st = dict(one, **{k: 1})

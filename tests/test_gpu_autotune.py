@@ -79,3 +79,32 @@ def test_thresholds_decide_the_split(gpu_lib, case, mode):
     if mode == "WORKLIST":
         assert out[256].jobs > 0 and out[256].tokens > 0
         assert out[1 << 24].jobs == 0 and out[1 << 24].tokens == 0
+
+
+def test_plans_cover_schedules_and_size_classes(gpu_lib, case):
+    g = updated(gpu_lib, case)
+    p, plans, trials, st = g.autotune_plans()
+    assert st.status == gpu_lib.OK
+    modes = set(plans[:, 0].tolist())
+    assert gpu_lib.WORKLIST in modes and gpu_lib.JACOBI in modes
+    assert len({int(x) for x in plans[plans[:, 0] == gpu_lib.WORKLIST, 1]}) >= 2   # grid sizes
+    assert np.all(np.isfinite(trials)) and np.all(trials > 0)
+    best = int(np.argmin(trials))
+    assert (p.mode, p.grid_ctas, p.gather_split, p.mark_split) == tuple(int(x) for x in plans[best])
+    assert np.max(np.abs(g.get_ranks() - case["ref1"])) <= LINF64
+    assert g.df_pagerank().processed == 0   # the pending set was consumed once
+
+
+def test_explicit_plans(gpu_lib, case):
+    g = updated(gpu_lib, case)
+    p, plans, trials, st = g.autotune_plans(plans=[(gpu_lib.JACOBI, 0, 0, 0)])
+    assert st.status == gpu_lib.OK and p.mode == gpu_lib.JACOBI and len(trials) == 1
+    assert np.max(np.abs(g.get_ranks() - case["ref1"])) <= LINF64
+    g2 = updated(gpu_lib, case)
+    p, plans, trials, st = g2.autotune_plans(plans=[(gpu_lib.WORKLIST, 16, 0, 0),
+                                                    (gpu_lib.ROUND, 0, 4096, 8192)])
+    assert st.status == gpu_lib.OK and len(trials) == 2
+    assert np.max(np.abs(g2.get_ranks() - case["ref1"])) <= LINF64
+    with pytest.raises(gpu_lib.DfprError) as e:
+        g2.autotune_plans(plans=[(gpu_lib.WORKLIST, 0, 0, 0)])   # nothing pending
+    assert e.value.status == gpu_lib.EINVAL
