@@ -760,6 +760,9 @@ def many_measure(args, quiet=False):
     s_set = dfpr.graph_load_parts(off.astype(np.int32), gsrc, gdst, cfg, stream=stream.cuda_stream)
     st0 = dfpr.static_pagerank(s_set, dfpr.default_params(mode=dfpr.JACOBI, tol=tol / 1000, max_iter=1000))
     R0 = dfpr.get_ranks(s_set)
+    # the set's update replays its device work from a CUDA graph (captured on
+    # the first update, again only when a plan changes the launch)
+    dfpr.set_capture(s_set, True)
     singles = []
     for i, (n, src, dst, frac, _) in enumerate(graphs):
         g = dfpr.graph_load(n, src, dst, cfg, stream=stream.cuda_stream)
@@ -824,6 +827,7 @@ def many_measure(args, quiet=False):
             set_kernel.append(st.ms)
             set_bytes.append(algorithmic_bytes(st.as_dict(), 8 if prec == dfpr.FP64 else 4))
     clk = clocks.stop()
+    cap_info = dfpr.capture_info(s_set)
     # both forms reach the same ranks (each graph's update is the same method)
     Rs = dfpr.get_ranks(s_set)
     in_off, in_idx = dfpr.get_csc(s_set)
@@ -860,6 +864,7 @@ def many_measure(args, quiet=False):
                    "sharding": "graphs to ranks by greedy balance of edge draws, no collective",
                    "precision": args.precision},
         "batched": {"ms_per_step": set_total / args.steps, "kernel_ms": kernel_total / args.steps,
+                    "update_from_cuda_graph": True, "captures_replays": list(cap_info),
                     "p50_ms": pct(set_lat, 50), "p99_ms": pct(set_lat, 99)},
         "per_graph_sequential": {"ms_per_step": single_total / args.steps,
                                  "p50_ms": pct(single_lat, 50), "p99_ms": pct(single_lat, 99)},
