@@ -546,7 +546,7 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}-batch{args.batch_frac:g}", "n": n, "m": m0,
                    "batch_edges": b, "insert_frac": 0.8, "precision": args.precision,
                    "mode": args.mode, "alpha": 0.85, "tol": tol,
-                   "accumulate": ("contributions as int64 round(C * 2^62), exact integer sums; "
+                   "accumulate": ("contributions as int64 round(C * 2^60), exact integer sums; "
                                   "ranks FP64" if args.precision == "fp64" else
                                   "FP32 contributions, TwoSum-compensated FP32 sums; FP64 "
                                   "dead-end sum, L-inf and normalisation"),

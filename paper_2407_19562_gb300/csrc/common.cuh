@@ -185,15 +185,18 @@ struct Pending {
 };
 
 // Contribution C[u] = R[u] / |out(u)| of a vertex, as stored for gathers.
-// FP64 graphs keep it as a 64-bit fixed-point number with scale 2^62, so a
+// FP64 graphs keep it as a 64-bit fixed-point number with scale 2^60, so a
 // gather sums exactly with integer adds (GB300's FP64 rate is a small
 // fraction of its integer and FP32 rates): each term is rounded once, to
-// 2^-63 absolute, and the sum of at most 1 (ranks sum to 1) cannot overflow.
+// 2^-61 absolute, and a sum stays below 8. Ranks never exceed 1 (the worklist
+// epilogue clamps transients there), so every term is at most 1 and a
+// vertex's in-sum reaches 8 only with more than 8 in-neighbours at rank 1,
+// i.e. a rank mass eight times the graph's total of 1.
 // FP32 graphs keep the float quotient.
-constexpr double kFix62 = 4611686018427387904.0;          // 2^62
-constexpr double kInvFix62 = 1.0 / 4611686018427387904.0;  // 2^-62
+constexpr double kFix = 1152921504606846976.0;          // 2^60
+constexpr double kInvFix = 1.0 / 1152921504606846976.0;  // 2^-60
 __device__ __forceinline__ long long contrib_of(double r, int d) {
-  return d > 0 ? __double2ll_rn((r / (double)d) * kFix62) : 0ll;
+  return d > 0 ? __double2ll_rn((r / (double)d) * kFix) : 0ll;
 }
 __device__ __forceinline__ float contrib_of(float r, int d) {
   return d > 0 ? __fdiv_rn(r, (float)d) : 0.f;
@@ -229,7 +232,7 @@ struct dfpr_graph {
   dfpr::Rows out, in;
   // ranks: FP64 or FP32 arrays (one of each pair is used)
   dfpr::DevArray<double> R64;              // rank
-  dfpr::DevArray<long long> C64;           // contribution R/outdeg, fixed point 2^-62
+  dfpr::DevArray<long long> C64;           // contribution R/outdeg, fixed point 2^-60
   dfpr::DevArray<float> R32, C32;
   dfpr::DevArray<dfpr::VRec> vrec;        // worklist: per-vertex records of the running call
   dfpr::DevArray<double> R64b;             // second vectors of the Jacobi schedule

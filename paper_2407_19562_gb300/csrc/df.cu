@@ -93,7 +93,7 @@ __device__ __forceinline__ long long atomic_add_ll_old(long long* p, long long v
 // Precision traits
 // ---------------------------------------------------------------------------
 
-// FP64 ranks; contributions in 64-bit fixed point (scale 2^62, see
+// FP64 ranks; contributions in 64-bit fixed point (scale 2^60, see
 // contrib_of), summed exactly with integer adds.
 struct P64 {
   using val = double;
@@ -102,7 +102,8 @@ struct P64 {
   static __device__ __forceinline__ acc zero() { return 0ll; }
   static __device__ __forceinline__ acc from(contrib x) { return x; }
   static __device__ __forceinline__ acc add(acc a, acc b) { return a + b; }
-  static __device__ __forceinline__ double total(acc a) { return __ll2double_rn(a) * kInvFix62; }
+  static __device__ __forceinline__ double total(acc a) { return __ll2double_rn(a) * kInvFix; }
+  static __device__ __forceinline__ double value(contrib c) { return __ll2double_rn(c) * kInvFix; }
   static __device__ __forceinline__ acc shfl_up(acc a, int d) { return __shfl_up_sync(kFull, a, d); }
   static __device__ __forceinline__ val load(const val* p) { return __ldcg(p); }
   static __device__ __forceinline__ contrib load_c(const contrib* p) { return __ldcg(p); }
@@ -143,7 +144,7 @@ struct P64 {
     atomicAdd(p, (unsigned long long)x);
   }
   static __device__ __forceinline__ double job_total(unsigned long long bits) {
-    return __ll2double_rn((long long)bits) * kInvFix62;
+    return __ll2double_rn((long long)bits) * kInvFix;
   }
   static constexpr bool relative = false;
 };
@@ -166,6 +167,7 @@ struct P32 {
     return {s, __fadd_rn(__fadd_rn(a.c, b.c), err)};
   }
   static __device__ __forceinline__ double total(acc a) { return (double)a.s + (double)a.c; }
+  static __device__ __forceinline__ double value(contrib c) { return (double)c; }
   static __device__ __forceinline__ acc shfl_up(acc a, int d) {
     return {__shfl_up_sync(kFull, a.s, d), __shfl_up_sync(kFull, a.c, d)};
   }
@@ -742,7 +744,9 @@ __device__ void expand_rows(const Args<P>& a, int v, int od, long long oo, int l
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       if (base + k * 32 >= total) break;  // warp-uniform
-      const bool need = mark_one(a, t[k], own[k] >= 0, wv[k]);
+      // the row owner's own self-loop is not marked: its rank is exact in itself
+      const int owner_v = __shfl_sync(kFull, v, own[k] >= 0 ? own[k] : 0);
+      const bool need = mark_one(a, t[k], own[k] >= 0 && t[k] != owner_v, wv[k]);
       buf_push(a, pb, t[k], need, true, lane, st);
     }
 #pragma unroll
@@ -831,20 +835,31 @@ __device__ __forceinline__ void note_done(const Args<P>& a, int v, int lane) {
 
 constexpr double kDriftFactor = 10.0;
 
-// Eq. 1 epilogue of one recomputed vertex v on the per-vertex record: new
-// rank r from the gathered sum; Delta r against the record's rank; the rank
-// at the last expansion (initialised to the rank at the call's start) decides
-// whether v marks its out-neighbours. Writes the record's rank and x, the
-// recomputed flag, and C.
+// Eq. 1 epilogue of one recomputed vertex v on the per-vertex record. Every
+// vertex of the worklist schedule has a self-loop (dead ends are removed that
+// way, Sec. 5.1.3), so its own rank is one of its inputs: r = b + alpha *
+// (S + r / |out(v)|), S the sum over its other in-edges. The epilogue solves
+// that term in closed form, r = (b + alpha * S) / (1 - alpha / |out(v)|), the
+// same fixed point as Eq. 1: v's recomputation is exact in its own rank, so
+// it never needs to revisit itself because its own rank moved (its expansion
+// marks its other out-neighbours only). sum is the gather over the whole
+// in-row, the self-loop included; its term is the stored contribution of
+// r_old. Delta r against the record's rank; the rank at the last expansion
+// (initialised to the rank at the call's start) decides whether v marks its
+// out-neighbours. Writes the record's rank and x, the recomputed flag, and C.
 template <class P>
 __device__ __forceinline__ void vertex_epilogue_rec(const Args<P>& a, int v, double sum,
                                                     typename P::val r_old, typename P::val x0,
                                                     unsigned fl, int od, double dangling,
                                                     bool& expand, bool& requeue, bool& fresh,
                                                     WarpStats& st) {
-  double s2 = sum;
-  if (a.teleport) s2 += dangling / (double)a.n;
-  const typename P::val r = (typename P::val)(base_of(a, v) + a.alpha * s2);
+  const double others = sum - P::value(contrib_of(r_old, od));
+  const double r_exact = (base_of(a, v) + a.alpha * others) / (1.0 - a.alpha / (double)od);
+  (void)dangling;  // the worklist schedule has no dead ends
+  // a rank is at most 1 at the fixed point; stale inputs of a vertex with few
+  // out-edges can push the closed form above it for a moment, and the
+  // fixed-point contributions must stay bounded
+  const typename P::val r = (typename P::val)fmin(fmax(r_exact, 0.0), 1.0);
   fresh = (fl & 1u) == 0u;
   const double dr = fabs((double)r - (double)r_old);
   a.C[v] = contrib_of(r, od);
@@ -973,7 +988,7 @@ __device__ void run_mark_token(const Args<P>& a, unsigned u, unsigned chunk, int
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       if (e0 + k * 32 >= end) break;  // warp-uniform
-      buf_push(a, pb, t[k], mark_one(a, t[k], t[k] >= 0, wv[k]), true, lane, st);
+      buf_push(a, pb, t[k], mark_one(a, t[k], t[k] >= 0 && t[k] != (int)u, wv[k]), true, lane, st);
     }
   }
   if (lane == 0) st.c[kStMarked] += (unsigned long long)max(0ll, end - beg);
