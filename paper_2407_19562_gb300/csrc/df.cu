@@ -147,6 +147,8 @@ struct P64 {
     return __ll2double_rn((long long)bits) * kInvFix;
   }
   static constexpr bool relative = false;
+  // the worklist epilogue solves the self-loop term of Eq. 1 in closed form
+  static constexpr bool closed_form = true;
 };
 
 // FP32 with compensated summation: every addition is an error-free TwoSum
@@ -208,6 +210,9 @@ struct P32 {
     return __longlong_as_double((long long)bits);
   }
   static constexpr bool relative = true;
+  // Eq. 1 as printed, the vertex's current rank in its self-loop term: FP32
+  // rounding jitter under a relative, one-ulp frontier floor needs that damping
+  static constexpr bool closed_form = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -744,9 +749,10 @@ __device__ void expand_rows(const Args<P>& a, int v, int od, long long oo, int l
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       if (base + k * 32 >= total) break;  // warp-uniform
-      // the row owner's own self-loop is not marked: its rank is exact in itself
+      // with the closed form, the row owner's own self-loop is not marked:
+      // its rank is exact in itself
       const int owner_v = __shfl_sync(kFull, v, own[k] >= 0 ? own[k] : 0);
-      const bool need = mark_one(a, t[k], own[k] >= 0 && t[k] != owner_v, wv[k]);
+      const bool need = mark_one(a, t[k], own[k] >= 0 && !(P::closed_form && t[k] == owner_v), wv[k]);
       buf_push(a, pb, t[k], need, true, lane, st);
     }
 #pragma unroll
@@ -838,51 +844,64 @@ constexpr double kDriftFactor = 10.0;
 // Eq. 1 epilogue of one recomputed vertex v on the per-vertex record. Every
 // vertex of the worklist schedule has a self-loop (dead ends are removed that
 // way, Sec. 5.1.3), so its own rank is one of its inputs: r = b + alpha *
-// (S + r / |out(v)|), S the sum over its other in-edges. The epilogue solves
-// that term in closed form, r = (b + alpha * S) / (1 - alpha / |out(v)|), the
-// same fixed point as Eq. 1: v's recomputation is exact in its own rank, so
-// it never needs to revisit itself because its own rank moved (its expansion
-// marks its other out-neighbours only). sum is the gather over the whole
-// in-row, the self-loop included; its term is the stored contribution of
-// r_old. Delta r against the record's rank; the rank at the last expansion
-// (initialised to the rank at the call's start) decides whether v marks its
-// out-neighbours. Writes the record's rank and x, the recomputed flag, and C.
+// (S + r / |out(v)|), S the sum over its other in-edges.
+//  - FP64 (P::closed_form) solves that term: r = (b + alpha * S) /
+//    (1 - alpha / |out(v)|), the same fixed point as Eq. 1. The recomputation
+//    is exact in v's own rank, so v never revisits itself because its own rank
+//    moved: its expansion marks its other out-neighbours only, and it is not
+//    queued again for its own change. The sums are exact integers and the
+//    frontier threshold is absolute, so rounding cannot move a rank by it.
+//  - FP32 evaluates Eq. 1 as printed, with v's current rank in the self term:
+//    a vertex whose rank moved marks itself (its self-loop) on expansion, and
+//    queues itself again while its own change is above tau. Under the relative
+//    tolerance with its one-ulp floor, the closed form's undamped rounding
+//    jitter let neighbours flip each other by an ulp or two for ever.
+// sum is the gather over the whole in-row, the self-loop included; the closed
+// form subtracts its term, the stored contribution of r_old. The rank at the
+// last expansion (initialised to the rank at the call's start) decides
+// whether v marks its out-neighbours. Writes the record's rank and x, the
+// recomputed flag, and C.
 template <class P>
 __device__ __forceinline__ void vertex_epilogue_rec(const Args<P>& a, int v, double sum,
                                                     typename P::val r_old, typename P::val x0,
                                                     unsigned fl, int od, double dangling,
                                                     bool& expand, bool& requeue, bool& fresh,
                                                     WarpStats& st) {
-  const double others = sum - P::value(contrib_of(r_old, od));
-  const double r_exact = (base_of(a, v) + a.alpha * others) / (1.0 - a.alpha / (double)od);
   (void)dangling;  // the worklist schedule has no dead ends
-  // a rank is at most 1 at the fixed point; stale inputs of a vertex with few
-  // out-edges can push the closed form above it for a moment, and the
-  // fixed-point contributions must stay bounded
-  const typename P::val r = (typename P::val)fmin(fmax(r_exact, 0.0), 1.0);
+  typename P::val r;
+  if constexpr (P::closed_form) {
+    const double others = sum - P::value(contrib_of(r_old, od));
+    const double r_exact = (base_of(a, v) + a.alpha * others) / (1.0 - a.alpha / (double)od);
+    // a rank is at most 1 at the fixed point; stale inputs of a vertex with
+    // few out-edges can push the closed form above it for a moment, and the
+    // fixed-point contributions must stay bounded
+    r = (typename P::val)fmin(fmax(r_exact, 0.0), 1.0);
+  } else {
+    r = (typename P::val)(base_of(a, v) + a.alpha * sum);
+  }
   fresh = (fl & 1u) == 0u;
   const double dr = fabs((double)r - (double)r_old);
   a.C[v] = contrib_of(r, od);
   const double thr_f = frontier_thr<P>(a.tol_f, r);
-  const double thr = P::relative ? a.tol * fabs((double)r) : a.tol;
   const double drift = fabs((double)r - (double)x0);
   expand = P::relative ? drift > thr_f : (dr > thr_f || drift > kDriftFactor * thr_f);
+  requeue = !P::closed_form && dr > (P::relative ? a.tol * fabs((double)r) : a.tol);
   P::store_rx(a.rec + v, r, expand ? r : x0);
   if (fresh) P::set_fresh(a.rec + v);
-  requeue = dr > thr;
   st.max_change = fmax(st.max_change, dr);
 }
 
 // After the epilogue of lane-local vertices: marks out-neighbours of expanding
-// ones, flags non-converged ones, and moves each from running to idle (or back
-// to queued when it was flagged meanwhile). Returns the number of vertices
-// that left the system (their `pending` units are owed).
+// ones, flags the vertices to requeue (FP32: own change above tau), and moves
+// each vertex from running to idle (or back to queued when it was flagged
+// meanwhile). Returns the number of vertices that left the system (their
+// `pending` units are owed).
 template <class P>
 __device__ int finish_vertices(const Args<P>& a, int v, bool expand, bool requeue, RowDesc orow,
                                int lane, int* s_excl, long long* s_off, PushBuf pb, WarpStats& st) {
   __threadfence();  // new ranks visible before neighbours are queued
   expand_rows(a, v, expand ? orow.deg : 0, orow.off, lane, s_excl, s_off, pb, st);
-  if (requeue && !expand) {  // not converged: flag itself so that the finish re-queues it
+  if (requeue && !expand) {  // flags itself so that the finish re-queues it
     const unsigned sh = (unsigned)(v & 15) * 2u;
     atomicOr(a.state + (v >> 4), 1u << sh);
   }
@@ -988,7 +1007,8 @@ __device__ void run_mark_token(const Args<P>& a, unsigned u, unsigned chunk, int
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       if (e0 + k * 32 >= end) break;  // warp-uniform
-      buf_push(a, pb, t[k], mark_one(a, t[k], t[k] >= 0 && t[k] != (int)u, wv[k]), true, lane, st);
+      buf_push(a, pb, t[k], mark_one(a, t[k], t[k] >= 0 && !(P::closed_form && t[k] == (int)u), wv[k]),
+               true, lane, st);
     }
   }
   if (lane == 0) st.c[kStMarked] += (unsigned long long)max(0ll, end - beg);
@@ -1047,7 +1067,21 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       sc[kStClock] = t;
     }
   };
+  unsigned polls = 0;
   while (!a.mark_only) {
+    // the stop conditions are also polled while work remains: a queue that
+    // does not drain must still end at the work cap or the time budget
+    if ((++polls & 15u) == 0u) {
+      int stop = 0;
+      if (lane == 0) {
+        if (ld_volatile(&ctl->abort)) stop = 1;
+        else if (timed_out(a)) {
+          stop_with(a, DFPR_ETIMEOUT);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(kFull, stop, 0)) break;
+    }
     const unsigned long long tok = pop_token(a, lane);
     if (tok != kNoToken) {
       const unsigned kind = (unsigned)(tok >> 62);
