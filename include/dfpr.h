@@ -493,9 +493,8 @@ dfpr_status dfpr_residual(const dfpr_graph* g, double alpha, double* linf, doubl
  * Scratch (a second rank vector, two contribution vectors and three control
  * words) lives in one fixed __device__ array of 24 MiB + 256 bytes that every
  * GPU loading this library keeps until the process exits. The first call on a
- * device looks up that array's device address (with the device current), so
- * make the first call before any stream capture; a cudaDeviceReset after it
- * invalidates the address. All calls share the array: calls that overlap on
+ * device looks up that array's device address (with the device current); a
+ * cudaDeviceReset after it invalidates the address. All calls share the array: calls that overlap on
  * the GPU race and give wrong results. Returns OK, ENOTCONV (cap reached;
  * ranks are the last iterate), EINVAL, ECUDA.
  */

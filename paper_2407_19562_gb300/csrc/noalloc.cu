@@ -21,8 +21,7 @@
 // Host code cannot use the array's symbol as a device address: on the host it
 // names a host-side stand-in. The device address is fetched once per device
 // with cudaGetSymbolAddress (with that device current) on the first call made
-// on that device, so that first call should happen before any stream capture.
-// The cached address belongs to the device's current context: a
+// on that device. The cached address belongs to the device's current context: a
 // cudaDeviceReset between calls (which also frees every other device
 // allocation of the process) invalidates it. Every call shares the array and
 // its previous contents: the control words are cleared before they are used,
