@@ -212,7 +212,7 @@ def host_residual(R, in_off, in_idx, part_off=None, alpha=0.85, sample=200_000, 
 NOMINAL_HBM_GBS = 7900.0  # HBM3e bandwidth of the part, for context (the roofline uses the measured copy)
 
 MEASURED_TRAFFIC = {
-    ("rmat24-batch0.0001", "fp64", "worklist"): ("587340b7ac61af66", 147.55e9),
+    ("rmat24-batch0.0001", "fp64", "worklist"): ("d553767e0905df7a", 101.53e9),
 }
 
 
@@ -238,31 +238,41 @@ def measured_traffic(workload, precision, mode):
     return rec[1]
 
 
-def random_line_ceiling(torch, dev, gib=4, count=1 << 26, reps=5):
-    """Random-access ceiling of the memory system: 8-byte gathers at uniformly
-    random positions of a gib-GiB array (far larger than L2), timed with CUDA
-    events (torch's index_select). Every gather costs one DRAM line fetch, so
-    the rate is the device's ceiling for scattered lines, the bound that the
-    DF kernel's contribution and state reads meet long before the copy
-    bandwidth."""
-    big = torch.zeros(gib << 27, dtype=torch.int64, device=dev)
-    idx = torch.randint(0, big.numel(), (count,), device=dev, dtype=torch.int64)
+def _random_gather_rate(torch, dev, elems, count, reps):
+    """Best rate (gathers/s) of torch's index_select of `count` random int64
+    from an array of `elems` int64, timed with CUDA events."""
+    src = torch.zeros(elems, dtype=torch.int64, device=dev)
+    idx = torch.randint(0, src.numel(), (count,), device=dev, dtype=torch.int64)
     out = torch.empty(count, dtype=torch.int64, device=dev)
-    torch.index_select(big, 0, idx, out=out)
+    torch.index_select(src, 0, idx, out=out)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     best = None
     for _ in range(reps):
         e0.record()
-        torch.index_select(big, 0, idx, out=out)
+        torch.index_select(src, 0, idx, out=out)
         e1.record()
         e1.synchronize()
         t = e0.elapsed_time(e1)
         best = t if best is None else min(best, t)
-    del big, idx, out
+    del src, idx, out
     torch.cuda.empty_cache()
-    rate = count / (best * 1e-3)
+    return count / (best * 1e-3)
+
+
+def random_line_ceiling(torch, dev, gib=4, count=1 << 26, reps=5, l2_mib=32):
+    """Random-access ceilings of the memory system: 8-byte gathers at uniformly
+    random positions (torch's index_select, CUDA events), once from a gib-GiB
+    array (far larger than L2: every gather costs one DRAM line fetch, the
+    device's ceiling for scattered lines) and once from an l2_mib-MiB array
+    that L2 holds (the ceiling for scattered 32-byte sectors served by L2).
+    The DF kernel's contribution and state reads meet these bounds long
+    before the copy bandwidth."""
+    rate = _random_gather_rate(torch, dev, gib << 27, count, reps)
+    l2_rate = _random_gather_rate(torch, dev, l2_mib << 17, count, reps)
     return {"lines_per_s": rate, "gb_s_at_64B_lines": rate * 64 / 1e9,
-            "how": f"index_select of {count} random int64 from a {gib} GiB array, best of {reps}"}
+            "how": f"index_select of {count} random int64 from a {gib} GiB array, best of {reps}",
+            "l2_sectors_per_s": l2_rate,
+            "l2_how": f"the same from a {l2_mib} MiB array (L2-resident)"}
 
 
 def load_peaks():

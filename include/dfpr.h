@@ -117,7 +117,7 @@ typedef struct dfpr_params {
   int32_t mode;        /* DFPR_MODE_* */
   int32_t normalize;   /* 1: rescale ranks to sum 1 (FP64 sum) after convergence */
   int32_t grid_ctas;   /* persistent grid size; 0 = the schedule's own: worklist about
-                          sqrt(n)/4 CTAs (at least 8, at most one wave on every SM),
+                          sqrt(n)/4 CTAs (at least 8, at most 4 per SM and one wave),
                           round at most n/2048, jacobi one wave */
   double timeout_ms;   /* wall-clock budget on the device; <= 0 means 60000 */
   /* Simulated faults (Sec. 5.1.6; experiments of Sec. 5.3 and 5.4). All 0 by
@@ -443,8 +443,8 @@ dfpr_status dfpr_graph_capture_info(const dfpr_graph* g, int64_t* captures, int6
  * schedule at the graph's own grid, at half of it and at a full wave (size
  * classes), at its own grid with split pairs (2048, 2048) and (16384, 16384)
  * (degree classes; pairs below the graph's minimum split are left out), and
- * the jacobi schedule (DF_BB, Alg. 1); teleport graphs: the jacobi schedule
- * alone. At most 8 built-in plans.
+ * the jacobi schedule (DF_BB, Alg. 1); repeated plans are timed once;
+ * teleport graphs: the jacobi schedule alone. At most 8 built-in plans.
  * p: in, the parameters of every trial; out, the same with the chosen plan's
  * four fields. Outputs (host, may be NULL): *n_run the plans timed;
  * plans_run[4 * n_run] those plans; trial_ms[n_run] their times (INFINITY

@@ -651,7 +651,8 @@ dfpr_status dfpr_autotune_plans(dfpr_graph* g, dfpr_params* p, int32_t n_plans,
   DeviceGuard dg(g->device);
   std::vector<int32_t> def;
   if (!plans) {
-    // size classes (worklist grid: the graph's own, half of it, a full wave),
+    // size classes (worklist grid: the graph's own rule, half of it, a full
+    // wave of the occupancy limit),
     // degree classes (split thresholds), and the barrier-based schedule
     const int rule = default_worklist_grid(g, *p);
     dfpr_params q = *p;
@@ -667,12 +668,18 @@ dfpr_status dfpr_autotune_plans(dfpr_graph* g, dfpr_params* p, int32_t n_plans,
              DFPR_MODE_WORKLIST, rule, 2048, 2048,
              DFPR_MODE_WORKLIST, rule, 16384, 16384,
              DFPR_MODE_JACOBI, 0, 0, 0};
-      // splits below the graph's minimum are left out
+      // splits below the graph's minimum are left out, and so are repeats
+      // (the rule's grid is a full wave on small devices)
       const long long min_split = std::max<long long>(256, (g->m + (1ll << 20) - 1) >> 20);
       std::vector<int32_t> keep;
-      for (size_t i = 0; i < def.size(); i += 4)
-        if ((def[i + 2] == 0 || def[i + 2] >= min_split) && (def[i + 3] == 0 || def[i + 3] >= min_split))
-          keep.insert(keep.end(), def.begin() + i, def.begin() + i + 4);
+      for (size_t i = 0; i < def.size(); i += 4) {
+        if ((def[i + 2] != 0 && def[i + 2] < min_split) || (def[i + 3] != 0 && def[i + 3] < min_split))
+          continue;
+        bool seen = false;
+        for (size_t j = 0; j < keep.size() && !seen; j += 4)
+          seen = std::equal(keep.begin() + j, keep.begin() + j + 4, def.begin() + i);
+        if (!seen) keep.insert(keep.end(), def.begin() + i, def.begin() + i + 4);
+      }
       def.swap(keep);
     }
     plans = def.data();

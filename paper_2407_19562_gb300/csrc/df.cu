@@ -1983,20 +1983,28 @@ int persistent_grid(dfpr_graph* g, const dfpr_params& p, const void* kernel) {
   return per_sm * g->sm_count;
 }
 
-// Grid of the worklist schedule: at most one wave, and about sqrt(n) / 4 CTAs
-// (at least 8). Every warp holds 32 vertices in flight; when the in-flight
-// set is a large share of the frontier, vertices are recomputed from inputs
-// that are about to change and are queued again. Measured on R-MAT graphs
-// with 16 draws per vertex, batch 1e-4 |E| (ms per update at a full wave of
-// 760 CTAs / at the grid this rule gives): scale 18, 18-23 / 12-16 (154
-// CTAs); scale 20, 30 / 22 (256); scale 22, 50 / 44-47 (512); scale 24 keeps
-// the full wave (112 ms; 141 ms at half of it).
+// Grid of the worklist schedule: about sqrt(n) / 4 CTAs (at least 8), and at
+// most 4 CTAs per SM (or the occupancy limit, if lower). Every warp holds 32
+// vertices in flight; when the in-flight set is a large share of the
+// frontier, vertices are recomputed from inputs that are about to change and
+// are queued again. Measured on R-MAT graphs with 16 draws per vertex, batch
+// 1e-4 |E|, FP64, ms per update (mean of 5-16 batches) at the grid given:
+//  - scale 20: 128 / 192 / 256 / 320 / 384 CTAs: 24 / 17 / 16 / 15 / 16 ms;
+//  - scale 22: 256 / 384 / 456 / 512 / 608 / 760: 31 / 33 / 30 / 24 / 35 / 38;
+//  - scale 23: 380 / 456 / 532 / 608 / 760: 42 / 47 / 49 / 50 / 54;
+//  - scale 24: 456 / 532 / 608 / 684 / 760: 84 / 70 / 55 / 69 / 75, the
+//    same minimum on a second seed (54 against 76 ms) and at 1e-3 |E|
+//    batches (90 against 99); at 1e-5 |E|, 65 against 63.
+// The time follows the work: at 4 CTAs per SM the scale-24 updates did
+// 5.3-8.4 n recomputations (10.1-10.6 n at 5 per SM), with fewer hub
+// recomputations and expansions; the dependence on the grid is not monotone.
 template <class P>
 int worklist_grid(dfpr_graph* g, const dfpr_params& p) {
   const int full = persistent_grid(g, p, (const void*)k_worklist<P>);
   if (p.grid_ctas > 0) return full;
+  const long long cap = std::min<long long>(full, 4ll * g->sm_count);
   const long long by_size = (long long)(0.25 * std::sqrt((double)g->n));
-  return (int)std::max<long long>(std::min<long long>(8, full), std::min<long long>(full, by_size));
+  return (int)std::max<long long>(std::min<long long>(8, cap), std::min<long long>(cap, by_size));
 }
 
 // Grid of the round schedule. One CTA per 2048 vertices at most: warps move
