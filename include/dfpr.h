@@ -132,11 +132,14 @@ typedef struct dfpr_params {
        stop taking part at a random batch boundary, without finishing any
        bookkeeping, like a thread that never runs again. The round schedule
        (Alg. 2) finishes without them: its passes and R_C flags let the
-       other warps recompute what they left. The worklist schedule keeps a
-       global count of open work that a crashed warp leaves unbalanced, so
-       it stops at timeout_ms with DFPR_ETIMEOUT (valid, partly updated
-       ranks). The jacobi schedule rejects crashes with DFPR_EINVAL: its
-       iteration barrier could never complete (Sec. 5.4).
+       other warps recompute what they left. The worklist schedule finishes
+       without them too while helping is on (see helping below): idle warps
+       return a crashed warp's claimed vertices to the queue. With helping
+       off, the crashed warp's claim keeps the global count of open work
+       unbalanced, so the call stops at timeout_ms with DFPR_ETIMEOUT
+       (valid, partly updated ranks). The jacobi schedule rejects crashes
+       with DFPR_EINVAL: its iteration barrier could never complete
+       (Sec. 5.4).
      Limits: 0 <= fault_delay_prob <= 1, 0 <= fault_delay_us <= 1e6,
      0 <= fault_crash_warps < the warps of the launch. */
   double fault_delay_prob;
@@ -153,6 +156,14 @@ typedef struct dfpr_params {
      dfpr_autotune picks them by timing. */
   int32_t gather_split;
   int32_t mark_split;
+  /* Helping (worklist schedule; Sec. 4.4: threads help each other so that a
+     slow or crashed thread does not hold up the rest). 1 (the default): every
+     warp publishes the vertices it claims, and an idle warp that sees the same
+     claim unchanged in two of its scans at least 10 ms apart returns those
+     vertices to the queue, so a crash-stopped warp's work is done by the
+     others. 0: off; a crashed warp's claim then keeps the update open until
+     timeout_ms. Other schedules ignore it. */
+  int32_t helping;
 } dfpr_params;
 
 /* Counters of one call. */

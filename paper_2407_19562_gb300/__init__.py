@@ -62,7 +62,8 @@ class Params(ctypes.Structure):
                 ("grid_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
                 ("fault_delay_prob", ctypes.c_double), ("fault_delay_us", ctypes.c_double),
                 ("fault_crash_warps", ctypes.c_int32), ("fault_seed", ctypes.c_uint32),
-                ("gather_split", ctypes.c_int32), ("mark_split", ctypes.c_int32)]
+                ("gather_split", ctypes.c_int32), ("mark_split", ctypes.c_int32),
+                ("helping", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -139,6 +139,7 @@ void check_params(const dfpr_params& p) {
                DFPR_EINVAL, "gather_split must be 0 or lie in [256, 2^24]");
   DFPR_REQUIRE(p.mark_split == 0 || (p.mark_split >= 256 && p.mark_split <= (1 << 24)),
                DFPR_EINVAL, "mark_split must be 0 or lie in [256, 2^24]");
+  DFPR_REQUIRE(p.helping == 0 || p.helping == 1, DFPR_EINVAL, "helping must be 0 or 1");
   DFPR_REQUIRE(!(p.fault_crash_warps > 0 && p.mode == DFPR_MODE_JACOBI), DFPR_EINVAL,
                "crash-stop faults need a lock-free schedule: the jacobi schedule's iteration "
                "barrier would never complete (Sec. 5.4)");
@@ -224,6 +225,7 @@ void dfpr_default_params(dfpr_params* p) {
   p->frontier_tol = 0.0;
   p->max_iter = 500;
   p->mode = DFPR_MODE_WORKLIST;
+  p->helping = 1;
   p->normalize = 0;
   p->grid_ctas = 0;
   p->timeout_ms = 60000.0;

@@ -285,6 +285,9 @@ struct Args {
   unsigned long long fault_perm_a, fault_perm_b;
   unsigned long long fault_warps;
   int fault_crash_warps;
+  // helping (worklist): per-warp hold records, kHoldWords 64-bit words each
+  unsigned long long* hold;
+  int helping;
 };
 
 // Per-warp statistics: counters in shared memory that lane 0 updates with
@@ -1015,6 +1018,80 @@ __device__ void run_mark_token(const Args<P>& a, unsigned u, unsigned chunk, int
   buf_flush(a, pb, lane, st);
 }
 
+// ---------------------------------------------------------------------------
+// Helping: the claimed vertices of a warp that stopped go back to the queue
+// ---------------------------------------------------------------------------
+
+// Every warp of a worklist launch keeps a hold record of kHoldWords 64-bit
+// words: [0] its claim word, launch generation << 32 | claim epoch << 1 |
+// holding; [1] a claim word a helper saw; [2] that helper's warp << 32 | its
+// scan count; [3] the time of that sighting; [4..19] the 32 vertex ids of the
+// warp's current batch. A warp publishes its batch right after claiming it
+// and clears the holding bit once the batch is finished. An idle warp scans
+// the records every kHelpScanEvery idle polls. A claim that the same helper
+// saw unchanged in two of its scans, at least kHelpAfterNs apart, belongs to
+// a warp that stopped (a batch takes well under a millisecond): the helper
+// takes the record with a compare-and-swap and puts its vertices back in the
+// queue with their open-work units. Both conditions are needed: the scan
+// count does not advance while the device is paused, and the clock does.
+constexpr int kHoldWords = 20;
+constexpr unsigned kHelpScanEvery = 4096;
+constexpr unsigned long long kHelpAfterNs = 10000000ull;
+
+// This warp's hold record.
+template <class P>
+__device__ __forceinline__ unsigned long long* hold_of(const Args<P>& a, int w) {
+  return a.hold + ((size_t)blockIdx.x * kWPB + (size_t)w) * kHoldWords;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *(const volatile unsigned long long*)p;
+}
+
+template <class P>
+__device__ __forceinline__ void help_stopped_warps(const Args<P>& a, unsigned long long gen, int me,
+                                                unsigned scan, int lane, PushBuf pb, WarpStats& st) {
+  const int warps = (int)gridDim.x * kWPB;
+  for (int base = 0; base < warps; base += 32) {
+    const int r = base + lane;
+    bool take = false;
+    if (r < warps && r != me) {
+      unsigned long long* rec = a.hold + (size_t)r * kHoldWords;
+      const unsigned long long word = ld_volatile_u64(rec);
+      if ((word >> 32) == gen && (word & 1ull)) {
+        const unsigned long long seen = ld_volatile_u64(rec + 1);
+        const unsigned long long who = ld_volatile_u64(rec + 2);
+        const unsigned long long now = gtime();
+        const unsigned long long since = now - ld_volatile_u64(rec + 3);
+        if (seen != word || ((int)(who >> 32) != me && since > 3 * kHelpAfterNs)) {
+          // first sighting of this claim (or its helper stopped too): note it
+          *(volatile unsigned long long*)(rec + 1) = word;
+          *(volatile unsigned long long*)(rec + 2) = ((unsigned long long)me << 32) | scan;
+          *(volatile unsigned long long*)(rec + 3) = now;
+        } else if ((int)(who >> 32) == me && scan - (unsigned)who >= 2u && since >= kHelpAfterNs) {
+          take = atomicCAS(rec, word, word & ~1ull) == word;
+        }
+      }
+    }
+    unsigned todo = __ballot_sync(kFull, take);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int* ids = reinterpret_cast<const int*>(a.hold + (size_t)(base + src) * kHoldWords + 4);
+      int v = ld_volatile(ids + lane);
+      if (v >= a.n) v = -1;  // only ids of this graph were ever published
+      if (v >= 0) {  // running (perhaps flagged) -> queued; its unit goes with it
+        const unsigned sh = (unsigned)(v & 15) * 2u;
+        atomicOr(a.state + (v >> 4), 1u << sh);
+        atomicAnd(a.state + (v >> 4), ~(2u << sh));
+      }
+      __threadfence();
+      buf_push(a, pb, v, v >= 0, false, lane, st);
+      buf_flush(a, pb, lane, st);
+    }
+  }
+}
+
 template <class P>
 __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   __shared__ int s_excl[kWPB][32];
@@ -1036,6 +1113,19 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
   unsigned long long* const sc = s_stat[w];  // lane 0: counters; kStProcessed = recomputations
                                              // not yet added to the work-cap count
   const PushBuf pb{s_push[w], &s_pcnt[w][0], &s_pcnt[w][1], &s_pcnt[w][2]};
+  // helping: the launch generation that tells this launch's hold records
+  // from earlier ones, and this warp's claim epoch, idle polls and scans
+  // (shared memory: they hold no registers)
+  __shared__ unsigned long long s_gen;
+  __shared__ unsigned s_help[kWPB][3];
+  if (a.helping) {
+    if (threadIdx.x == 0) s_gen = (ctl->t_start >> 10) & 0xffffffffull;
+    if (lane == 0) {
+      s_help[w][0] = s_help[w][1] = s_help[w][2] = 0u;
+    }
+    __syncthreads();
+    if (lane == 0) *(volatile unsigned long long*)hold_of(a, w) = s_gen << 32;
+  }
   auto mark = [&](int t, bool valid) {
     const unsigned word = valid ? ld_volatile(a.state + (t >> 4)) : 0u;
     const bool need = mark_one(a, t, valid, word);
@@ -1127,6 +1217,12 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
         }
       }
       if (__shfl_sync(kFull, stop, 0)) break;
+      if (a.helping) {
+        unsigned scan = 0;
+        if (lane == 0 && ++s_help[w][1] % kHelpScanEvery == 0u) scan = ++s_help[w][2];
+        scan = __shfl_sync(kFull, scan, 0);
+        if (scan) help_stopped_warps(a, s_gen, (int)blockIdx.x * kWPB + w, scan, lane, pb, st);
+      }
       __nanosleep(backoff);
       backoff = min(backoff * 2, 1024u);
       phase_mark(0);
@@ -1157,6 +1253,14 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
       }
     }
     if (!__all_sync(kFull, ok)) break;
+    if (a.helping) {  // publish the batch (after settling this warp's earlier completions)
+      settle_owed(a, pb, lane);
+      unsigned long long* my = hold_of(a, w);
+      reinterpret_cast<int*>(my + 4)[lane] = v;
+      __syncwarp();
+      if (lane == 0)
+        *(volatile unsigned long long*)my = (s_gen << 32) | ((unsigned long long)(++s_help[w][0] & 0x7fffffffu) << 1) | 1ull;
+    }
     if (a.fault_crash_warps &&
         fault_crash(a, __shfl_sync(kFull, lane == 0 ? sc[kStBatches] : 0ull, 0)))
       return;  // crash-stop holding claimed vertices (Sec. 5.4)
@@ -1210,6 +1314,9 @@ __global__ void __launch_bounds__(kNT, 5) k_worklist(Args<P> a) {
     stats_count(st, kStExpansions, expand, lane);
     phase_mark(2);
     const int done = finish_vertices(a, v, expand, requeue, orow, lane, s_excl[w], s_off[w], pb, st);
+    if (a.helping && lane == 0)  // the batch is finished: no longer holding
+      *(volatile unsigned long long*)hold_of(a, w) =
+          (s_gen << 32) | ((unsigned long long)(s_help[w][0] & 0x7fffffffu) << 1);
     note_done(a, v, lane);
     phase_mark(3);
     const unsigned proc_b = __ballot_sync(kFull, v >= 0);
@@ -1939,6 +2046,8 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
                       : (unsigned long long)(p.fault_delay_prob * 18446744073709551616.0);
   a.fault_delay_ns = (unsigned long long)(p.fault_delay_us * 1000.0);
   a.fault_crash_warps = p.fault_crash_warps;
+  a.hold = nullptr;
+  a.helping = 0;
   a.fault_perm_a = 1;
   a.fault_perm_b = 0;
   a.fault_warps = 1;
@@ -2189,6 +2298,17 @@ dfpr_status run_worklist(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr
   Args<P> a = make_args<P>(g, p);
   set_vectors<P>(g, a);
   a.mark_only = mark_only ? 1 : 0;
+  if (p.helping && !mark_only) {  // hold records for every warp of the launch
+    const size_t words = (size_t)worklist_grid<P>(g, p) * kWPB * kHoldWords;
+    if (g->hold.count < words) {
+      g->hold.reset(words, s);
+      // a record is read only while its generation is this launch's; zeros
+      // belong to no launch
+      DFPR_CUDA(cudaMemsetAsync(g->hold.p, 0, words * sizeof(unsigned long long), s));
+    }
+    a.hold = g->hold.p;
+    a.helping = 1;
+  }
   if (g->capture && kind == kRunDF && !mark_only && !a.teleport && s != nullptr && kernel_ms) {
     run_captured_update<P>(g, p, a, kernel_ms);
   } else {

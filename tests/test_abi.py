@@ -53,7 +53,7 @@ int main(void) {
          sizeof(dfpr_stats));
   F(dfpr_graph_config, tail_slack); F(dfpr_params, timeout_ms); F(dfpr_params, grid_ctas);
   F(dfpr_params, fault_delay_prob); F(dfpr_params, fault_crash_warps); F(dfpr_params, fault_seed);
-  F(dfpr_params, gather_split); F(dfpr_params, mark_split);
+  F(dfpr_params, gather_split); F(dfpr_params, mark_split); F(dfpr_params, helping);
   F(dfpr_stats, passes); F(dfpr_stats, residual_linf); F(dfpr_stats, ms);
   return 0;
 }
@@ -68,7 +68,8 @@ int main(void) {
     assert int(got["dfpr_graph_config.tail_slack"]) == dfpr.Config.tail_slack.offset
     assert int(got["dfpr_params.timeout_ms"]) == dfpr.Params.timeout_ms.offset
     assert int(got["dfpr_params.grid_ctas"]) == dfpr.Params.grid_ctas.offset
-    for f in ("fault_delay_prob", "fault_crash_warps", "fault_seed", "gather_split", "mark_split"):
+    for f in ("fault_delay_prob", "fault_crash_warps", "fault_seed", "gather_split", "mark_split",
+              "helping"):
         assert int(got[f"dfpr_params.{f}"]) == getattr(dfpr.Params, f).offset
     assert int(got["dfpr_stats.passes"]) == dfpr.Stats.passes.offset
     assert int(got["dfpr_stats.residual_linf"]) == dfpr.Stats.residual_linf.offset
@@ -81,6 +82,7 @@ def test_defaults_are_the_papers_constants():
     assert p.frontier_tol == 0.0  # selects tol / 1000 (Sec. 4.5)
     assert p.mode == dfpr.WORKLIST
     assert p.fault_delay_prob == 0.0 and p.fault_delay_us == 0.0 and p.fault_crash_warps == 0
+    assert p.helping == 1  # warps help a stopped warp (Sec. 4.4)
     c = dfpr.default_config()
     assert c.precision == dfpr.FP64 and c.dead_end == dfpr.SELF_LOOPS
 

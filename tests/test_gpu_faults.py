@@ -5,11 +5,14 @@ a batch of vertices; a crash-stop is a warp that returns at a random batch
 boundary without finishing its bookkeeping. Nothing here faults or hangs the
 GPU: every wait in the kernels is bounded by the call's time budget.
 
-Expected behaviour, as in the paper: the lock-free round schedule (Alg. 2)
-finishes with the same accuracy despite delays and crashes; the barrier-based
-jacobi schedule tolerates delays but cannot complete with a crashed thread
-(it rejects the request); the worklist schedule tolerates delays, and a crash
-leaves its count of open work unbalanced, so it stops at the time budget.
+Expected behaviour, as in the paper: the lock-free schedules finish with the
+same accuracy despite delays and crashes. The round schedule (Alg. 2) does so
+through its passes and R_C flags; the worklist schedule through helping (Sec.
+4.4): idle warps return the claimed vertices of a warp that stopped to the
+queue. With helping off, a crashed worklist warp leaves the count of open work
+unbalanced, so the call stops at the time budget (a bounded wait that runs
+out). The barrier-based jacobi schedule tolerates delays but cannot complete
+with a crashed thread (it rejects the request).
 """
 import numpy as np
 import pytest
@@ -72,10 +75,26 @@ def test_delays_keep_accuracy(gpu_lib, case, mode):
     assert st.ms >= 0.3  # at least one 300-us sleep happened
 
 
-def test_worklist_crash_stops_at_the_time_budget_and_recovers(gpu_lib, case):
+@pytest.mark.parametrize("crashed", [1, WARPS // 2, WARPS - 1])
+def test_worklist_finishes_despite_crashes(gpu_lib, case, crashed):
+    """Helping: the vertices a crashed warp held go back to the queue."""
+    g = updated_graph(gpu_lib, case)
+    st = g.df_pagerank(params(gpu_lib, "WORKLIST", fault_crash_warps=crashed, fault_seed=5))
+    assert st.status == gpu_lib.OK
+    assert np.max(np.abs(g.get_ranks() - case["ref1"])) <= LINF64
+
+
+def test_worklist_static_finishes_despite_crashes(gpu_lib, case):
+    g = gpu_lib.graph_load(case["n"], case["src"], case["dst"])
+    st = g.static_pagerank(params(gpu_lib, "WORKLIST", fault_crash_warps=WARPS // 2, fault_seed=3))
+    assert st.status == gpu_lib.OK
+    assert np.max(np.abs(g.get_ranks() - case["ref0"])) <= LINF64
+
+
+def test_worklist_crash_without_helping_stops_at_the_time_budget_and_recovers(gpu_lib, case):
     g = updated_graph(gpu_lib, case)
     st = g.df_pagerank(params(gpu_lib, "WORKLIST", fault_crash_warps=WARPS // 2, fault_seed=5,
-                              timeout_ms=300.0))
+                              timeout_ms=300.0, helping=0))
     assert st.status == gpu_lib.ETIMEOUT
     st = g.nd_pagerank(gpu_lib.default_params())  # the graph stays usable
     assert st.status == gpu_lib.OK
@@ -88,7 +107,8 @@ def test_jacobi_rejects_crashes_and_bad_fault_parameters(gpu_lib, case):
            dict(mode="ROUND", fault_delay_prob=1.5),
            dict(mode="ROUND", fault_delay_us=2e6),
            dict(mode="ROUND", fault_crash_warps=-1),
-           dict(mode="ROUND", fault_crash_warps=WARPS)]  # every warp of the launch
+           dict(mode="ROUND", fault_crash_warps=WARPS),  # every warp of the launch
+           dict(mode="WORKLIST", helping=2)]
     for kw in bad:
         mode = kw.pop("mode")
         with pytest.raises(gpu_lib.DfprError) as e:
@@ -105,6 +125,6 @@ def test_same_seed_same_crashing_warps(gpu_lib, case):
     for _ in range(2):
         g = updated_graph(gpu_lib, case)
         st = g.df_pagerank(params(gpu_lib, "WORKLIST", fault_crash_warps=WARPS - 1, fault_seed=9,
-                                  timeout_ms=200.0))
+                                  timeout_ms=200.0, helping=0))
         out.append(st.status)
     assert out == [gpu_lib.ETIMEOUT, gpu_lib.ETIMEOUT]
