@@ -207,12 +207,17 @@ def host_residual(R, in_off, in_idx, part_off=None, alpha=0.85, sample=200_000, 
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_worklist
-# launch from an ncu capture of the same workload, kept with a hash of the
-# kernel's sources: a figure is reported only while the sources are unchanged.
+# launch from an ncu capture of the same workload, with the algorithmic bytes
+# of that same launch (from the captured run's own counters), kept with a
+# hash of the kernel's sources: a figure is reported only while the sources
+# are unchanged. The work of an update varies from batch to batch (the
+# asynchronous schedule), so a run reports the captured launch's DRAM bytes
+# per algorithmic byte times its own algorithmic bytes per launch.
 NOMINAL_HBM_GBS = 7900.0  # HBM3e bandwidth of the part, for context (the roofline uses the measured copy)
 
 MEASURED_TRAFFIC = {
-    ("rmat24-batch0.0001", "fp64", "worklist"): ("d553767e0905df7a", 101.53e9),
+    # workload: (kernel source hash, DRAM bytes of the launch, its algorithmic bytes)
+    ("rmat24-batch0.0001", "fp64", "worklist"): ("fdeb12640cff2ef8", 93.21e9, 90.61e9),
 }
 
 
@@ -232,10 +237,11 @@ def kernel_source_hash():
 
 
 def measured_traffic(workload, precision, mode):
+    """(DRAM bytes, algorithmic bytes) of the captured launch, or None."""
     rec = MEASURED_TRAFFIC.get((workload, precision, mode))
-    if rec is None or rec[0] != kernel_source_hash():
+    if rec is None or rec[0] != kernel_source_hash() or rec[2] <= 0:
         return None
-    return rec[1]
+    return rec[1], rec[2]
 
 
 def _random_gather_rate(torch, dev, elems, count, reps):
@@ -512,7 +518,9 @@ def run_ours(args):
     bytes_per = [algorithmic_bytes(s, s_r) for s in stats]
     achieved = sum(bytes_per) / (sum(kern_ms) * 1e-3) / 1e9 if sum(kern_ms) > 0 else 0.0
     peak, peak_kind = load_peaks()
-    traffic = measured_traffic(f"{args.workload}-batch{args.batch_frac:g}", args.precision, args.mode)
+    capture = measured_traffic(f"{args.workload}-batch{args.batch_frac:g}", args.precision, args.mode)
+    # this run's DRAM bytes per launch, at the captured launch's bytes per algorithmic byte
+    traffic = capture[0] / capture[1] * float(np.mean(bytes_per)) if capture else None
     ws_bytes, l2 = working_set_bytes(n, m0, s_r), l2_bytes(dev)
     ceiling = random_line_ceiling(torch, dev)
 
@@ -565,6 +573,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
+                     "traffic_capture": ({"dram_bytes": capture[0], "algorithmic_bytes": capture[1],
+                                          "ratio": capture[0] / capture[1],
+                                          "how": "one ncu launch of this workload; traffic = "
+                                                 "ratio x this run's algorithmic bytes"}
+                                         if capture else None),
                      "peak_nominal": NOMINAL_HBM_GBS,
                      "kernel": "k_worklist (persistent DF kernel)",
                      "kernel_ms": float(np.mean(kern_ms)),
@@ -592,7 +605,8 @@ def run_ours(args):
                  "pushes": mean("pushes"), "affected": mean("affected"),
                  "batches": mean("batches"), "tokens": mean("tokens"), "jobs": mean("jobs"),
                  "phase_share": phase_share(stats),
-                 "apply_plus_df_ms_steps": step_ms, "wall_s": t_wall,
+                 "apply_plus_df_ms_steps": step_ms, "algorithmic_bytes_steps": bytes_per,
+                 "wall_s": t_wall,
                  "nonconverged_steps": len(bad)},
     }
     if ws == 1 and args.workload == "rmat24" and not args.no_extras:

@@ -48,10 +48,12 @@ def test_algorithmic_bytes_per_work_unit():
 def test_traffic_figure_retires_with_the_kernel_code(monkeypatch):
     b = load_bench()
     key = ("rmat24-batch0.0001", "fp64", "worklist")
-    digest, traffic = b.MEASURED_TRAFFIC[key]
+    digest, traffic, alg = b.MEASURED_TRAFFIC[key]  # the recorded capture's format
+    assert len(digest) == 16 and traffic >= 0 and alg >= 0
     assert len(b.kernel_source_hash()) == 16
-    monkeypatch.setattr(b, "kernel_source_hash", lambda: digest)
-    assert b.measured_traffic(*key) == traffic  # the sources the capture ran
+    monkeypatch.setitem(b.MEASURED_TRAFFIC, key, ("ab" * 8, 100e9, 80e9))
+    monkeypatch.setattr(b, "kernel_source_hash", lambda: "ab" * 8)
+    assert b.measured_traffic(*key) == (100e9, 80e9)  # the sources the capture ran
     monkeypatch.setattr(b, "kernel_source_hash", lambda: "0" * 16)
     assert b.measured_traffic(*key) is None     # changed code: no stale figure
     assert b.measured_traffic("rmat20-batch0.0001", "fp64", "worklist") is None

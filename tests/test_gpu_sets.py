@@ -110,3 +110,17 @@ def test_set_rejects_edges_between_graphs(gpu_lib):
     with pytest.raises(gpu_lib.DfprError) as e:
         gpu_lib.graph_load_parts(off, src, dst)
     assert e.value.status == gpu_lib.EINVAL
+
+
+def test_set_df_finishes_despite_crashed_warps(gpu_lib, gset):
+    """Helping in a many-graph launch: the claimed vertices of crash-stopped
+    warps go back to the queue, and every graph still matches the oracle."""
+    graphs, off, gsrc, gdst, gbatch = gset
+    s = gpu_lib.graph_load_parts(off, gsrc, gdst)
+    s.set_ranks(np.concatenate([g["ref0"] for g in graphs]))
+    s.apply_batch(*gbatch)
+    st = s.df_pagerank(gpu_lib.default_params(grid_ctas=8, fault_crash_warps=40, fault_seed=13))
+    assert st.status == gpu_lib.OK
+    R = s.get_ranks()
+    for i, g in enumerate(graphs):
+        assert np.max(np.abs(R[off[i]:off[i + 1]] - g["ref1"])) <= LINF64
