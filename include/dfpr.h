@@ -317,7 +317,14 @@ dfpr_status dfpr_nd_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* st
  */
 dfpr_status dfpr_static_pagerank(dfpr_graph* g, const dfpr_params* p, dfpr_stats* stats);
 
-/* Copies the n ranks out as FP64 (host or device; FP32 ranks are widened). */
+/* Copies the n ranks out as FP64 (host or device; FP32 ranks are widened),
+ * in the caller's vertex numbering. out: n doubles, caller-owned; on_device
+ * 1: a device pointer on the graph's device, 0: host memory. Page-locked
+ * host memory the device can address (cudaMallocHost, cudaHostAlloc, mapped
+ * registrations) is written directly by the device; other host memory goes
+ * through a device staging vector of n doubles that the graph keeps after
+ * the first such call. Returns when the ranks are in `out`. Errors: EINVAL
+ * (NULL argument), EBUSY, ECUDA. */
 dfpr_status dfpr_get_ranks(const dfpr_graph* g, double* out, int on_device);
 
 /* Replaces the n ranks (host or device FP64), e.g. to resume from saved ranks. */

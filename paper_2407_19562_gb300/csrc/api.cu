@@ -754,20 +754,30 @@ dfpr_status dfpr_get_ranks(const dfpr_graph* gc, double* out, int on_device) {
     DFPR_CUDA(cudaMemcpyAsync(out, g->R64.p, sizeof(double) * n,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   } else {
-    DevArray<double> tmp;
     double* dst = out;
+    bool stage = false;
     if (!on_device) {
-      tmp.reset((size_t)n, s);
-      dst = tmp.p;
+      // page-locked host memory that the device can address is written by
+      // the kernel itself; other host memory goes through a staging vector
+      // kept with the graph
+      cudaPointerAttributes attr;
+      if (cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+          attr.devicePointer) {
+        dst = static_cast<double*>(attr.devicePointer);
+      } else {
+        cudaGetLastError();  // an unregistered pointer is not an error here
+        if (g->rank_stage.count < (size_t)n) g->rank_stage.reset((size_t)n, s);
+        dst = g->rank_stage.p;
+        stage = true;
+      }
     }
     if (g->cfg.precision == DFPR_FP64)
       k_ranks_out<double><<<blocks_for(n, kNT, sm_cap(16u)), kNT, 0, s>>>(g->R64.p, perm, dst, n);
     else
       k_ranks_out<float><<<blocks_for(n, kNT, sm_cap(16u)), kNT, 0, s>>>(g->R32.p, perm, dst, n);
     DFPR_LAUNCHED();
-    if (!on_device)
+    if (stage)
       DFPR_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    DFPR_CUDA(cudaStreamSynchronize(s));
   }
   DFPR_CUDA(cudaStreamSynchronize(s));
   return DFPR_OK;

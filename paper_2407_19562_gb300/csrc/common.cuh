@@ -236,6 +236,7 @@ struct dfpr_graph {
   dfpr::DevArray<float> R32, C32;
   dfpr::DevArray<dfpr::VRec> vrec;        // worklist: per-vertex records of the running call
   dfpr::DevArray<unsigned long long> hold;  // worklist: per-warp hold records (helping)
+  dfpr::DevArray<double> rank_stage;         // get_ranks into pageable host memory
   dfpr::DevArray<double> R64b;             // second vectors of the Jacobi schedule
   dfpr::DevArray<long long> C64b;
   dfpr::DevArray<float> R32b, C32b;
