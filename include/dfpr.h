@@ -148,7 +148,9 @@ typedef struct dfpr_params {
   uint32_t fault_seed;
   /* Degree classes: an in-row longer than gather_split edges is summed as
      gather_split-edge tokens that any warp takes (worklist and round
-     schedules), and an out-row longer than mark_split edges is marked the
+     schedules; the jacobi schedule sums such rows in gather_split-edge
+     chunks spread over every warp after each iteration's shorter rows), and
+     an out-row longer than mark_split edges is marked the
      same way (worklist schedule); shorter rows are gathered and marked by one
      warp, edge-balanced over its 32 vertices. 0 selects the defaults (4096
      and 8192); otherwise max(256, edges / 2^20) <= value <= 2^24, so that

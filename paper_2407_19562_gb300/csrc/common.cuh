@@ -168,6 +168,8 @@ struct DfCtl {
   unsigned int abort;              // 1: workers stop
   unsigned long long edges, expansions, edges_marked, pushes, affected;
   unsigned long long max_change_bits;  // max |change| of a recomputation (bits of a double)
+  long long nheavy;                // jacobi: long in-rows registered this iteration
+  long long heavy_chunks;          // jacobi: their gather_split-edge chunks
   long long work_cap;              // cap on recomputations (worklist)
   unsigned long long t_start;      // globaltimer at launch
   double dsum;                     // rank held by dead ends (teleport)
@@ -237,6 +239,10 @@ struct dfpr_graph {
   dfpr::DevArray<dfpr::VRec> vrec;        // worklist: per-vertex records of the running call
   dfpr::DevArray<unsigned long long> hold;  // worklist: per-warp hold records (helping)
   dfpr::DevArray<double> rank_stage;         // get_ranks into pageable host memory
+  dfpr::DevArray<int32_t> jh_v;             // jacobi: long in-rows of an iteration (vertex,
+  dfpr::DevArray<int32_t> jh_rem;           //   chunks not yet summed,
+  dfpr::DevArray<unsigned long long> jh_sum;  //   partial sums,
+  dfpr::DevArray<long long> jh_off;         //   chunk offsets)
   dfpr::DevArray<double> R64b;             // second vectors of the Jacobi schedule
   dfpr::DevArray<long long> C64b;
   dfpr::DevArray<float> R32b, C32b;

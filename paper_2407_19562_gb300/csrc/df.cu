@@ -48,7 +48,7 @@ constexpr int kWPB = kNT / 32;
 constexpr int kMarkChunk = 1024;  // out-edges per marking item
 
 // Scratch slots (see common.cuh; graph.cu uses 0..28).
-enum { kSMarkCnt = 30, kSMarkOff = 31 };
+enum { kSMarkCnt = 30, kSMarkOff = 31, kSListKeys = 32, kSListTmp = 33 };
 
 #define GRID_STRIDE(i, n)                                                             \
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
@@ -288,6 +288,13 @@ struct Args {
   // helping (worklist): per-warp hold records, kHoldWords 64-bit words each
   unsigned long long* hold;
   int helping;
+  // jacobi: in-rows longer than gather_split, registered per iteration and
+  // summed in gather_split-edge chunks by every warp (jh_cap slots)
+  int32_t* jh_v;
+  int32_t* jh_rem;
+  unsigned long long* jh_sum;
+  long long* jh_off;
+  long long jh_cap;
 };
 
 // Per-warp statistics: counters in shared memory that lane 0 updates with
@@ -1358,7 +1365,9 @@ __device__ void mark_round(const Args<P>& a, int t, bool valid, int lane) {
   long long nc_add = 0;
   if (valid) {
     const uint32_t bit = 1u << (t & 31);
-    fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
+    // affected bits only grow during a call: a set bit needs no atomic
+    if ((ld_volatile(a.va_bits + (t >> 5)) & bit) == 0u)
+      fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
     nc_add = (atomicOr(a.rc_bits + (t >> 5), bit) & bit) == 0u ? 1 : 0;
   }
   const unsigned b = __ballot_sync(kFull, fresh);
@@ -1657,6 +1666,59 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
 // Jacobi schedule: one iteration over a vertex list (or all vertices)
 // ---------------------------------------------------------------------------
 
+// Marks the out-neighbours of an expanding vertex (lane-local v, expand) as
+// affected from the next iteration on: a bit in va_bits, and the affected
+// list grows past the current count (warp-uniform call).
+template <class P>
+__device__ void jacobi_mark(const Args<P>& a, bool expand, int v, int lane, int* s_excl,
+                            long long* s_off, WarpStats& st) {
+  int od = 0;
+  long long oo = 0;
+  if (expand) {
+    const RowDesc r = a.out_rows[v];
+    od = r.deg;
+    oo = r.off;
+  }
+  int incl = od;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  __syncwarp();
+  s_excl[lane] = incl - od;
+  s_off[lane] = oo;
+  __syncwarp();
+  for (int base = 0; base < total; base += 32) {
+    const int e = base + lane;
+    const bool valid = e < total;
+    int t = 0;
+    if (valid) {
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_excl[mid] <= e) lo = mid; else hi = mid;
+      }
+      t = a.out_edges[s_off[lo] + (e - s_excl[lo])];
+    }
+    // affected from the next iteration on: the list grows past `count`
+    bool fresh = false;
+    if (valid) {
+      const uint32_t bit = 1u << (t & 31);
+      // affected bits only grow during a call: a set bit needs no atomic
+      if ((ld_volatile(a.va_bits + (t >> 5)) & bit) == 0u)
+        fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
+    }
+    const unsigned bb = __ballot_sync(kFull, fresh);
+    long long base2 = 0;
+    if (lane == 0 && bb) base2 = atomic_add_ll_old(&a.ctl->len.v, __popc(bb));
+    base2 = __shfl_sync(kFull, base2, 0);
+    if (fresh) a.alist[base2 + __popc(bb & lanemask_lt())] = t;
+  }
+  if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
+}
+
 template <class P>
 __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val* __restrict__ Rin,
                                                 const typename P::contrib* __restrict__ Cin,
@@ -1677,8 +1739,23 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
   const double dangling = a.teleport ? a.ctl->dsum : 0.0;
   for (long long bi = (long long)blockIdx.x * kWPB + w; bi < nbatch; bi += (long long)gridDim.x * kWPB) {
     const long long j = bi * 32 + lane;
-    const int v = j < count ? (list ? list[j] : (int)j) : -1;
-    const typename P::acc acc = gather(b, v, lane, s_excl[w], s_off[w], s_acc[w], st);
+    int v = j < count ? (list ? list[j] : (int)j) : -1;
+    RowDesc row;
+    row.off = 0;
+    row.deg = 0;
+    if (v >= 0) row = load_row(a.in_rows + v);
+    if (a.jh_v && row.deg > a.gather_split) {
+      // a long in-row: summed in chunks by every warp of k_jacobi_heavy
+      const long long slot = atomic_add_ll_old(&a.ctl->nheavy, 1);
+      if (slot < a.jh_cap) {
+        a.jh_v[slot] = v;
+        a.jh_rem[slot] = (row.deg + a.gather_split - 1) / a.gather_split;
+        a.jh_sum[slot] = 0ull;
+        v = -1;
+        row.deg = 0;
+      }
+    }
+    const typename P::acc acc = gather_row(b, row.deg, row.off, lane, s_excl[w], s_off[w], s_acc[w], st);
     bool expand = false;
     if (v >= 0) {
       const typename P::val r = finish_rank(b, acc, dangling, v);
@@ -1691,55 +1768,138 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
       st.max_change = fmax(st.max_change, dr);
     }
     stats_count(st, kStExpansions, expand, lane);
-    if (frontier) {
-      int od = 0;
-      long long oo = 0;
-      if (expand) {
-        const RowDesc r = a.out_rows[v];
-        od = r.deg;
-        oo = r.off;
-      }
-      int incl = od;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        int y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += y;
-      }
-      const int total = __shfl_sync(kFull, incl, 31);
-      __syncwarp();
-      s_excl[w][lane] = incl - od;
-      s_off[w][lane] = oo;
-      __syncwarp();
-      for (int base = 0; base < total; base += 32) {
-        const int e = base + lane;
-        const bool valid = e < total;
-        int t = 0;
-        if (valid) {
-          int lo = 0, hi = 32;
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_excl[w][mid] <= e) lo = mid; else hi = mid;
-          }
-          t = a.out_edges[s_off[w][lo] + (e - s_excl[w][lo])];
-        }
-        // affected from the next iteration on: the list grows past `count`
-        bool fresh = false;
-        if (valid) {
-          const uint32_t bit = 1u << (t & 31);
-          fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
-        }
-        const unsigned bb = __ballot_sync(kFull, fresh);
-        long long base2 = 0;
-        if (lane == 0 && bb) base2 = atomic_add_ll_old(&a.ctl->len.v, __popc(bb));
-        base2 = __shfl_sync(kFull, base2, 0);
-        if (fresh) a.alist[base2 + __popc(bb & lanemask_lt())] = t;
-      }
-      if (lane == 0) st.c[kStMarked] += (unsigned long long)total;
-    }
+    if (frontier) jacobi_mark(a, expand, v, lane, s_excl[w], s_off[w], st);
     if (lane == 0) atomicAdd(&a.ctl->processed.v, (unsigned long long)min(32ll, count - bi * 32));
     fault_delay(a, (unsigned long long)bi, v >= 0, lane);
   }
   flush_stats(a, st, lane);
+}
+
+// Chunk offsets of the long in-rows registered by k_jacobi (one block):
+// jh_off[h] = chunks of slots before h; the total goes to ctl->heavy_chunks.
+__global__ void __launch_bounds__(1024) k_jacobi_heavy_scan(DfCtl* ctl, const int32_t* __restrict__ rem,
+                                                            long long* __restrict__ off, long long cap) {
+  __shared__ long long s_w[32];
+  __shared__ long long s_carry;
+  const long long nh = min(ctl->nheavy, cap);
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (t == 0) s_carry = 0;
+  __syncthreads();
+  for (long long base = 0; base < nh; base += 1024) {
+    const long long i = base + t;
+    const long long x = i < nh ? (long long)rem[i] : 0ll;
+    long long incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long y = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      long long v = s_w[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const long long y = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += y;
+      }
+      s_w[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    const long long before = (wid ? s_w[wid - 1] : 0ll) + s_carry;
+    if (i < nh) off[i] = before + incl - x;
+    __syncthreads();
+    if (t == 0) s_carry += s_w[31];
+    __syncthreads();
+  }
+  if (t == 0) ctl->heavy_chunks = s_carry;
+}
+
+// The long in-rows of a Jacobi iteration: every warp takes gather_split-edge
+// chunks of them (grid-stride over all chunks), adds each chunk's sum into
+// the row's slot, and the warp that adds the last chunk finishes the vertex
+// (Eq. 1, change, frontier marking), as k_jacobi does for the rest.
+template <class P>
+__global__ void __launch_bounds__(kNT) k_jacobi_heavy(Args<P> a, const typename P::val* __restrict__ Rin,
+                                                      const typename P::contrib* __restrict__ Cin,
+                                                      typename P::val* __restrict__ Rout,
+                                                      typename P::contrib* __restrict__ Cout,
+                                                      int frontier) {
+  __shared__ int s_excl[kWPB][32];
+  __shared__ long long s_off[kWPB][32];
+  __shared__ unsigned long long s_stat[kWPB][kStCount];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpStats st;
+  stats_init(st, s_stat[w], lane);
+  const long long nh = min(a.ctl->nheavy, a.jh_cap);
+  const long long total = a.ctl->heavy_chunks;
+  const double dangling = a.teleport ? a.ctl->dsum : 0.0;
+  for (long long item = (long long)blockIdx.x * kWPB + w; item < total;
+       item += (long long)gridDim.x * kWPB) {
+    long long lo = 0, hi = nh;  // last slot h with jh_off[h] <= item
+    while (hi - lo > 1) {
+      const long long mid = (lo + hi) >> 1;
+      if (a.jh_off[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int v = a.jh_v[lo];
+    const RowDesc row = load_row(a.in_rows + v);
+    const long long beg = (item - a.jh_off[lo]) * a.gather_split;
+    const long long end = min((long long)row.deg, beg + a.gather_split);
+    typename P::acc acc = P::zero();
+    for (long long e0 = beg; e0 < end; e0 += 32 * kUnroll) {
+      typename P::contrib xv[kUnroll];
+      int uid[kUnroll];
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const long long e = e0 + k * 32 + lane;
+        uid[k] = e < end ? __ldg(a.in_edges + row.off + e) : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) xv[k] = uid[k] >= 0 ? P::load_c(Cin + uid[k]) : (typename P::contrib)0;
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) acc = P::add(acc, P::from(xv[k]));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc = P::add(acc, P::shfl_xor(acc, d));
+    int last = 0;
+    if (lane == 0) {
+      P::job_add(a.jh_sum + lo, acc);
+      fence_acq_rel();
+      last = atomicSub(a.jh_rem + lo, 1) == 1;
+      st.c[kStEdges] += (unsigned long long)max(0ll, end - beg);
+    }
+    if (!__shfl_sync(kFull, last, 0)) continue;
+    fence_acq_rel();
+    bool expand = false;
+    const int vv = lane == 0 ? v : -1;
+    if (vv >= 0) {
+      double sum = P::job_total(ld_volatile_u64(a.jh_sum + lo));
+      if (a.teleport) sum += dangling / (double)a.n;
+      const typename P::val r = (typename P::val)(base_of(a, vv) + a.alpha * sum);
+      const double dr = fabs((double)r - (double)Rin[vv]);
+      const int od = a.out_rows[vv].deg;
+      Rout[vv] = r;
+      Cout[vv] = contrib_of(r, od);
+      expand = frontier && dr > frontier_thr<P>(a.tol_f, r);
+      st.max_change = fmax(st.max_change, dr);
+    }
+    stats_count(st, kStExpansions, expand, lane);
+    if (frontier) jacobi_mark(a, expand, vv, lane, s_excl[w], s_off[w], st);
+  }
+  flush_stats(a, st, lane);
+}
+
+// The affected list's new entries as sort keys, and back (Jacobi schedule:
+// an iteration reads and writes separate vectors, so the order in which it
+// visits the affected vertices is free; ascending ids keep rows and ranks of
+// neighbouring list entries in the same sectors).
+__global__ void k_list_widen(const int32_t* __restrict__ list, long long n,
+                             unsigned long long* __restrict__ keys) {
+  GRID_STRIDE(i, n) keys[i] = (unsigned long long)(unsigned)list[i];
+}
+__global__ void k_list_narrow(const unsigned long long* __restrict__ keys, long long n,
+                              int32_t* __restrict__ list) {
+  GRID_STRIDE(i, n) list[i] = (int32_t)keys[i];
 }
 
 // Initial marking for the Jacobi schedule: affected list + bitmap.
@@ -1753,7 +1913,9 @@ __global__ void __launch_bounds__(kNT) k_mark_list(Args<P> a) {
     bool fresh = false;
     if (valid) {
       const uint32_t bit = 1u << (t & 31);
-      fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
+      // affected bits only grow during a call: a set bit needs no atomic
+      if ((ld_volatile(a.va_bits + (t >> 5)) & bit) == 0u)
+        fresh = (atomicOr(a.va_bits + (t >> 5), bit) & bit) == 0u;
     }
     const unsigned b = __ballot_sync(kFull, fresh);
     long long base = 0;
@@ -2048,6 +2210,11 @@ Args<P> make_args(dfpr_graph* g, const dfpr_params& p) {
   a.fault_crash_warps = p.fault_crash_warps;
   a.hold = nullptr;
   a.helping = 0;
+  a.jh_v = nullptr;
+  a.jh_rem = nullptr;
+  a.jh_sum = nullptr;
+  a.jh_off = nullptr;
+  a.jh_cap = 0;
   a.fault_perm_a = 1;
   a.fault_perm_b = 0;
   a.fault_warps = 1;
@@ -2497,6 +2664,20 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
     count = (long long)read_word(g, &g->ctl.p->len.v, sizeof(long long));
   }
   const int grid = persistent_grid(g, p, (const void*)k_jacobi<P>);
+  {  // slots for the long in-rows of an iteration: at most m / gather_split
+    const long long cap = g->m / a.gather_split + 2;
+    if ((long long)g->jh_v.count < cap) {
+      g->jh_v.reset((size_t)cap, s);
+      g->jh_rem.reset((size_t)cap, s);
+      g->jh_sum.reset((size_t)cap, s);
+      g->jh_off.reset((size_t)cap, s);
+    }
+    a.jh_v = g->jh_v.p;
+    a.jh_rem = g->jh_rem.p;
+    a.jh_sum = g->jh_sum.p;
+    a.jh_off = g->jh_off.p;
+    a.jh_cap = (long long)g->jh_v.count;
+  }
   const unsigned long long fault_seed0 = a.fault_seed;
   // DF with teleport dead ends: every rank holds alpha * D / n, D the dead-end
   // mass. Ranks outside the affected set were computed with D_last; once the
@@ -2510,6 +2691,9 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
   int it = 0;
   double last = 0.0;
   bool converged = false;
+  long long sorted_upto = 0;  // the list's prefix already in ascending id order
+  int id_bits = 1;
+  while (id_bits < 31 && (1ll << id_bits) < (long long)g->n) ++id_bits;
   for (; it < p.max_iter; ++it) {
     DFPR_CUDA(cudaMemsetAsync(&g->ctl.p->max_change_bits, 0, sizeof(unsigned long long), s));
     if (a.teleport) {
@@ -2524,9 +2708,26 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
       if (!(p.alpha * std::fabs(D - D_last) / (double)g->n <= shift_tol)) all = true;  // NaN: unknown
     }
     const bool listed = df && !all;
+    if (listed && count > sorted_upto) {  // entries appended since the last sort
+      const long long k = count - sorted_upto;
+      int32_t* seg = g->affected_list.p + sorted_upto;
+      unsigned long long* keys = g->scratch.get<unsigned long long>(kSListKeys, (size_t)k, s);
+      unsigned long long* tmp = g->scratch.get<unsigned long long>(kSListTmp, (size_t)k, s);
+      k_list_widen<<<grid_small(k), kNT, 0, s>>>(seg, k, keys);
+      DFPR_LAUNCHED();
+      unsigned long long* sorted = radix_sort_u64(keys, tmp, k, id_bits, g->scratch, s);
+      k_list_narrow<<<grid_small(k), kNT, 0, s>>>(sorted, k, seg);
+      DFPR_LAUNCHED();
+      sorted_upto = count;
+    }
     a.fault_seed = host_mix64(fault_seed0 + (unsigned long long)it);  // fresh delay draws per iteration
+    DFPR_CUDA(cudaMemsetAsync(&g->ctl.p->nheavy, 0, sizeof(long long), s));
     k_jacobi<P><<<grid, kNT, 0, s>>>(a, a.R, a.C, R2, C2, listed ? g->affected_list.p : nullptr,
                                      listed ? count : (long long)g->n, listed ? 1 : 0);
+    DFPR_LAUNCHED();
+    k_jacobi_heavy_scan<<<1, 1024, 0, s>>>(g->ctl.p, a.jh_rem, a.jh_off, a.jh_cap);
+    DFPR_LAUNCHED();
+    k_jacobi_heavy<P><<<grid, kNT, 0, s>>>(a, a.R, a.C, R2, C2, listed ? 1 : 0);
     DFPR_LAUNCHED();
     DFPR_CUDA(cudaMemcpyAsync(g->pinned, &g->ctl.p->max_change_bits, sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, s));

@@ -212,6 +212,27 @@ def test_df_jacobi_matches_oracle_df_bb(gpu_lib, c1):
     assert np.max(np.abs(g.get_ranks() - R_o)) <= 1e-13
 
 
+@pytest.mark.parametrize("split", [256, 1024])
+def test_df_jacobi_split_rows_match_oracle_df_bb(gpu_lib, c1, split):
+    """Long in-rows summed in chunks by many warps (every in-row above `split`
+    edges): the same iterations, affected set and values as the oracle's
+    DF_BB; the integer fixed-point sums make the chunk order irrelevant."""
+    g = gpu_lib.graph_load(c1["n"], c1["src"], c1["dst"])
+    indeg = np.diff(g.get_csc()[0])
+    assert (indeg > split).sum() >= 4  # the case has split rows
+    g.set_ranks(c1["R0"])
+    g.apply_batch(*c1["batch"])
+    st = g.df_pagerank(gpu_lib.default_params(mode=gpu_lib.JACOBI, gather_split=split))
+    R_o, st_o = c1["g1"].df_bb(c1["R0"])
+    assert st.passes == st_o.iterations
+    assert st.affected == st_o.affected
+    assert np.max(np.abs(g.get_ranks() - R_o)) <= 1e-13
+    # static (every vertex, every iteration) with split rows
+    st = g.static_pagerank(gpu_lib.default_params(mode=gpu_lib.JACOBI, gather_split=split))
+    assert st.status == gpu_lib.OK
+    assert np.max(np.abs(g.get_ranks() - c1["ref1"])) <= LINF64
+
+
 def test_df_after_gpu_static(gpu_lib, c1):
     """The whole path on the GPU: static ranks, batch, DF."""
     g = gpu_lib.graph_load(c1["n"], c1["src"], c1["dst"])
