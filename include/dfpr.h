@@ -149,7 +149,8 @@ typedef struct dfpr_params {
   /* Degree classes: an in-row longer than gather_split edges is summed as
      gather_split-edge tokens that any warp takes (worklist and round
      schedules; the jacobi schedule sums such rows in gather_split-edge
-     chunks spread over every warp after each iteration's shorter rows), and
+     chunks, 2048 by default, spread over every warp after each iteration's
+     shorter rows), and
      an out-row longer than mark_split edges is marked the
      same way (worklist schedule); shorter rows are gathered and marked by one
      warp, edge-balanced over its 32 vertices. 0 selects the defaults (4096
