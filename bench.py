@@ -217,7 +217,7 @@ NOMINAL_HBM_GBS = 7900.0  # HBM3e bandwidth of the part, for context (the roofli
 
 MEASURED_TRAFFIC = {
     # workload: (kernel source hash, DRAM bytes of the launch, its algorithmic bytes)
-    ("rmat24-batch0.0001", "fp64", "worklist"): ("1bab319a0acdb2d7", 77.06e9, 73.45e9),
+    ("rmat24-batch0.0001", "fp64", "worklist"): ("e43bc7b452f5cb31", 59.47e9, 55.94e9),
 }
 
 

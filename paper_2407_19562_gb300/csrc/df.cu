@@ -1667,6 +1667,18 @@ __global__ void __launch_bounds__(kNT) k_round(Args<P> a) {
 // Jacobi schedule: one iteration over a vertex list (or all vertices)
 // ---------------------------------------------------------------------------
 
+// Jacobi schedule: whether v marks its out-neighbours now. The affected set
+// only grows during a call and out-rows do not change, so once v has marked
+// them all, marking them again changes nothing: v marks on its first
+// expansion only (rc_bits, unused by this schedule, record it; they are
+// cleared with the affected list at the end of the call).
+template <class P>
+__device__ __forceinline__ bool first_expansion(const Args<P>& a, int v) {
+  const uint32_t bit = 1u << (v & 31);
+  if (ld_volatile(a.rc_bits + (v >> 5)) & bit) return false;
+  return (atomicOr(a.rc_bits + (v >> 5), bit) & bit) == 0u;
+}
+
 // Marks the out-neighbours of an expanding vertex (lane-local v, expand) as
 // affected from the next iteration on: a bit in va_bits, and the affected
 // list grows past the current count (warp-uniform call).
@@ -1765,7 +1777,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi(Args<P> a, const typename P::val
       Rout[v] = r;
       Cout[v] = contrib_of(r, od);
       const double thr_f = frontier_thr<P>(a.tol_f, r);
-      expand = frontier && dr > thr_f;
+      expand = frontier && dr > thr_f && first_expansion(a, v);
       st.max_change = fmax(st.max_change, dr);
     }
     stats_count(st, kStExpansions, expand, lane);
@@ -1881,7 +1893,7 @@ __global__ void __launch_bounds__(kNT) k_jacobi_heavy(Args<P> a, const typename 
       const int od = a.out_rows[vv].deg;
       Rout[vv] = r;
       Cout[vv] = contrib_of(r, od);
-      expand = frontier && dr > frontier_thr<P>(a.tol_f, r);
+      expand = frontier && dr > frontier_thr<P>(a.tol_f, r) && first_expansion(a, vv);
       st.max_change = fmax(st.max_change, dr);
     }
     stats_count(st, kStExpansions, expand, lane);
@@ -2759,7 +2771,7 @@ dfpr_status run_jacobi(dfpr_graph* g, const dfpr_params& p, RunKind kind, dfpr_s
     st->affected = df && !all ? count : g->n;
   }
   if (df) {
-    k_clear_list<<<grid_small(count), kNT, 0, s>>>(g->affected_list.p, count, g->va_bits.p, nullptr);
+    k_clear_list<<<grid_small(count), kNT, 0, s>>>(g->affected_list.p, count, g->va_bits.p, g->rc_bits.p);
     DFPR_LAUNCHED();
   }
   return converged ? DFPR_OK : DFPR_ENOTCONV;
