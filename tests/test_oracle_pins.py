@@ -562,3 +562,43 @@ def test_df_lf_tight_tolerance_matches_dense_solve():
     R, st = g1.df_lf(R_ref0, tol=1e-14)
     assert st.converged
     assert np.max(np.abs(R - exact)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Invariance under relabelling
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_relabelling_permutes_ranks_and_work(seed):
+    """Eq. 1 does not depend on vertex names: relabelling the graph, the batch
+    and the starting ranks by a permutation permutes every rank, and leaves
+    the DF iteration count and affected-set size unchanged. A mistake that
+    ties a quantity to a vertex's position rather than to the vertex (an
+    offset or degree read at the wrong index) breaks this."""
+    rng = np.random.default_rng(seed)
+    n, src, dst = workloads.rmat_graph(8, 8, 10 + seed)
+    batch = workloads.uniform_batch(n, 40, 20 + seed, src, dst)
+    perm = rng.permutation(n).astype(np.int32)
+    g0 = oracle.Graph.build(n, src, dst)
+    h0 = oracle.Graph.build(n, perm[src], perm[dst])
+    R, _ = g0.reference()
+    Rh, _ = h0.reference()
+    assert np.max(np.abs(Rh[perm] - R)) <= 1e-15
+    S, st = g0.static_bb()
+    Sh, sth = h0.static_bb()
+    assert st.iterations == sth.iterations
+    assert np.max(np.abs(Sh[perm] - S)) <= 1e-15
+    g1, nreal = g0.apply(*batch)
+    h1, nreal_h = h0.apply(*[perm[np.asarray(x, np.int64)] for x in batch])
+    assert nreal == nreal_h
+    R0h = np.empty(n)
+    R0h[perm] = R
+    for algo in ("df_bb", "df_lf"):
+        D, sd = getattr(g1, algo)(R)
+        Dh, sdh = getattr(h1, algo)(R0h)
+        assert sd.affected == sdh.affected
+        if algo == "df_bb":  # deterministic Jacobi iterations
+            assert sd.iterations == sdh.iterations
+            assert np.max(np.abs(Dh[perm] - D)) <= 1e-15
+        else:  # Alg. 2 visits vertices in id order: a different order, the same fixed point
+            assert np.max(np.abs(Dh[perm] - D)) <= 1e-9
